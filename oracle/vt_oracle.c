@@ -1,0 +1,695 @@
+/*
+ * vt_oracle.c -- plain, slow, FP64 CPU reference ("oracle") for differentiable
+ * volume rendering by ray traversal of a 3D Voronoi diagram.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only tests/, __graft_entry__.smoke() and bench.py's
+ * cpu_baseline / reference leg may load this library. The CUDA library never
+ * links, calls or includes anything from here, and this file includes nothing
+ * from the CUDA library: the two share no code, headers or constants.
+ *
+ * Everything is computed in double precision on double inputs (the Python
+ * wrapper promotes the FP32 scene and rays exactly). The oracle follows the
+ * plain definitions of the paper:
+ *   - Voronoi cell V_i = points nearest site p_i (Sec. 3.1).
+ *   - Start cell = nearest site of the ray origin, by brute force over all
+ *     sites (Sec. 3.1, "single nearest-neighbor query"); ties -> lowest id.
+ *   - Exit from cell i = nearest forward crossing of the bisector planes with
+ *     the Delaunay neighbours j (Sec. 3.1 and its walk figure):
+ *       t_j = n.((s_i+s_j)/2 - o) / (n.d),  n = s_j - s_i, only n.d > 0.
+ *   - Piecewise-constant volume rendering (Sec. 3.2):
+ *       alpha_k = 1 - exp(-sigma_{i_k} delta_k), T_{k+1} = T_k (1 - alpha_k),
+ *       C = sum_k T_k alpha_k c_k + T_final * bg,
+ *     stopping after the cell at which T < T_eps (early termination, Sec. 3.2).
+ *   - Colour = bilinear fetch of the cell's R x R octahedral texture at the
+ *     ray direction (Sec. 5.1 octahedral map, read "at the ray direction").
+ *   - Backward: analytic adjoint of the above from the stored segment list
+ *     (density gradient consistent with Eq. 3; plane-crossing gradient by
+ *     differentiating t_j with respect to both sites).
+ *   - Ray generation for pinhole, equidistant fisheye, rolling-shutter and
+ *     thin-lens cameras (Sec. 6.5 and the application appendix).
+ *
+ * Readings where the paper is silent (each listed in the design notes):
+ *   sign(0) = +1 in the lower-hemisphere unfold; texel coordinates clamp to
+ *   the edge; exact t ties keep the lower CSR position; termination is tested
+ *   after compositing the current cell; the background is added with the final
+ *   transmittance; skip rule "w < skip_weight -> no colour, keep T".
+ *
+ * Parity pins for every function live in tests/test_oracle_pins.py. The
+ * skip_weight > 0 rule is "parity unpinned" against the paper (the paper
+ * prints only PSNR deltas for it); it is pinned only against its own
+ * definition.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define VTO_OK 0
+#define VTO_ERR_ARG 1
+#define VTO_ERR_MEM 3
+
+/* per-ray flag bits (degenerate band, see vto_params.band_eps) */
+#define VTO_F_NEAR_EDGE 1    /* exit point within band_eps of another plane   */
+#define VTO_F_NEAR_ORIGIN 2  /* origin within band_eps of a plane of its cell */
+#define VTO_F_NEAR_CLIP 4    /* a crossing within band_eps of t_near'/t_far'  */
+#define VTO_F_T_AMBIG 8      /* |T/T_eps - 1| < 1e-4 at some composited step  */
+#define VTO_F_SKIP_AMBIG 16  /* |w/skip - 1| < 1e-4 at some step (skip > 0)   */
+#define VTO_F_MAX_STEPS 32   /* walk exceeded max_steps                       */
+#define VTO_F_BAD_RAY 64     /* zero / non-finite direction                   */
+
+typedef struct {
+  double t_near, t_far;
+  int32_t use_clip_box;
+  double clip_lo[3], clip_hi[3];
+  double T_eps;
+  double skip_weight;
+  double bg[3];
+  int32_t max_steps;
+  double band_eps;
+} vto_params;
+
+typedef struct {
+  int64_t n;
+  const double* sites; /* [n,3]        */
+  const double* sigma; /* [n]          */
+  const double* tex;   /* [n,R,R,3]    */
+  int32_t R;
+  const int64_t* off; /* [n+1]        */
+  const int32_t* idx; /* [E]          */
+} vto_scene;
+
+/* ------------------------------------------------------------------ */
+/* Octahedral map, Sec. 5.1: l1-normalise, upper hemisphere maps to the
+ * central diamond, lower hemisphere is unfolded to the corners.        */
+int vto_oct(const double d[3], double uv[2]) {
+  double l1 = fabs(d[0]) + fabs(d[1]) + fabs(d[2]);
+  if (!(l1 > 0.0) || !isfinite(l1)) return VTO_ERR_ARG;
+  double qx = d[0] / l1, qy = d[1] / l1;
+  if (d[2] >= 0.0) {
+    uv[0] = qx;
+    uv[1] = qy;
+  } else {
+    double sx = (qx >= 0.0) ? 1.0 : -1.0; /* sign(0) = +1 (reading) */
+    double sy = (qy >= 0.0) ? 1.0 : -1.0;
+    uv[0] = (1.0 - fabs(qy)) * sx;
+    uv[1] = (1.0 - fabs(qx)) * sy;
+  }
+  return VTO_OK;
+}
+
+/* Bilinear taps: (u,v) in [-1,1]^2 rescaled to texel space, texel centres at
+ * integer coordinates, clamp to edge (reading). Texel index = y*R + x.      */
+void vto_bilinear_taps(int32_t R, double u, double v, int64_t idx[4], double w[4]) {
+  double x = (u + 1.0) * 0.5 * R - 0.5;
+  double y = (v + 1.0) * 0.5 * R - 0.5;
+  if (x < 0.0) x = 0.0;
+  if (x > R - 1.0) x = R - 1.0;
+  if (y < 0.0) y = 0.0;
+  if (y > R - 1.0) y = R - 1.0;
+  int64_t x0 = (int64_t)floor(x), y0 = (int64_t)floor(y);
+  if (x0 > R - 1) x0 = R - 1;
+  if (y0 > R - 1) y0 = R - 1;
+  int64_t x1 = x0 + 1 < R ? x0 + 1 : R - 1;
+  int64_t y1 = y0 + 1 < R ? y0 + 1 : R - 1;
+  double fx = x - (double)x0, fy = y - (double)y0;
+  idx[0] = y0 * R + x0;
+  idx[1] = y0 * R + x1;
+  idx[2] = y1 * R + x0;
+  idx[3] = y1 * R + x1;
+  w[0] = (1.0 - fx) * (1.0 - fy);
+  w[1] = fx * (1.0 - fy);
+  w[2] = (1.0 - fx) * fy;
+  w[3] = fx * fy;
+}
+
+/* Cell colour at direction d: bilinear fetch of texture of `cell`. */
+static void cell_colour(const vto_scene* sc, int64_t cell, const int64_t taps[4], const double tw[4],
+                        double c[3]) {
+  const double* t = sc->tex + cell * (int64_t)sc->R * sc->R * 3;
+  c[0] = c[1] = c[2] = 0.0;
+  for (int q = 0; q < 4; ++q)
+    for (int ch = 0; ch < 3; ++ch) c[ch] += tw[q] * t[taps[q] * 3 + ch];
+}
+
+/* Brute-force nearest site (Sec. 3.1 cell definition); ties -> lowest id. */
+int64_t vto_nearest(int64_t n, const double* sites, const double q[3]) {
+  int64_t best = -1;
+  double bd = INFINITY;
+  for (int64_t i = 0; i < n; ++i) {
+    double dx = q[0] - sites[3 * i], dy = q[1] - sites[3 * i + 1], dz = q[2] - sites[3 * i + 2];
+    double dd = dx * dx + dy * dy + dz * dz;
+    if (dd < bd) {
+      bd = dd;
+      best = i;
+    }
+  }
+  return best;
+}
+
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+/* distance from x to the bisector plane of sites a, b */
+static double plane_dist(const double* sa, const double* sb, const double x[3]) {
+  double n[3] = {sb[0] - sa[0], sb[1] - sa[1], sb[2] - sa[2]};
+  double m[3] = {0.5 * (sa[0] + sb[0]), 0.5 * (sa[1] + sb[1]), 0.5 * (sa[2] + sb[2])};
+  double xm[3] = {x[0] - m[0], x[1] - m[1], x[2] - m[2]};
+  return fabs(dot3(n, xm)) / sqrt(dot3(n, n));
+}
+
+/* One walked cell of a ray. */
+typedef struct {
+  int64_t cell;
+  double t_in, t_out; /* walked parameter interval; t_out = +inf if unbounded */
+  int64_t next;       /* exit neighbour, -1 if none                             */
+  double a, b;        /* composited interval (clipped); composited iff b > a   */
+  int32_t composited, coloured;
+  double delta, alpha, T_before, w;
+  double c[3];
+} vto_seg;
+
+typedef struct {
+  vto_seg* s;
+  int64_t n, cap;
+} seg_buf;
+
+static int seg_push(seg_buf* b, const vto_seg* s) {
+  if (b->n == b->cap) {
+    int64_t nc = b->cap ? 2 * b->cap : 64;
+    vto_seg* ns = (vto_seg*)realloc(b->s, (size_t)nc * sizeof(vto_seg));
+    if (!ns) return VTO_ERR_MEM;
+    b->s = ns;
+    b->cap = nc;
+  }
+  b->s[b->n++] = *s;
+  return VTO_OK;
+}
+
+/* Clip [t_near, t_far] against the optional axis-aligned box (slab test). */
+static void clip_extent(const vto_params* p, const double o[3], const double d[3], double* t0,
+                        double* t1) {
+  double a = p->t_near, b = p->t_far;
+  if (p->use_clip_box) {
+    for (int k = 0; k < 3; ++k) {
+      if (d[k] != 0.0) {
+        double ta = (p->clip_lo[k] - o[k]) / d[k], tb = (p->clip_hi[k] - o[k]) / d[k];
+        double lo = ta < tb ? ta : tb, hi = ta < tb ? tb : ta;
+        if (lo > a) a = lo;
+        if (hi < b) b = hi;
+      } else if (o[k] < p->clip_lo[k] || o[k] > p->clip_hi[k]) {
+        b = a; /* parallel to the slab and outside: miss */
+      }
+    }
+  }
+  *t0 = a;
+  *t1 = b;
+}
+
+/* Walk and composite one ray. Fills the segment list, colour, transmittance,
+ * visited-cell count and band flags. Returns VTO_OK or VTO_ERR_MEM.        */
+static int walk_ray(const vto_scene* sc, const vto_params* p, const double o[3], const double d[3],
+                    seg_buf* segs, double C[3], double* T_out, int32_t* steps, int32_t* flags,
+                    int64_t* last_next, double* last_t_out) {
+  segs->n = 0;
+  *flags = 0;
+  C[0] = C[1] = C[2] = 0.0;
+  *T_out = 1.0;
+  *steps = 0;
+  *last_next = -1;
+  *last_t_out = INFINITY;
+  double dn = sqrt(dot3(d, d));
+  if (!(dn > 0.0) || !isfinite(dn)) {
+    *flags |= VTO_F_BAD_RAY;
+    return VTO_OK;
+  }
+  double t0, t1;
+  clip_extent(p, o, d, &t0, &t1);
+  if (!(t1 > t0)) {
+    for (int ch = 0; ch < 3; ++ch) C[ch] = p->bg[ch];
+    return VTO_OK;
+  }
+  double uv[2];
+  vto_oct(d, uv);
+  int64_t taps[4];
+  double tw[4];
+  vto_bilinear_taps(sc->R, uv[0], uv[1], taps, tw);
+
+  int64_t cell = vto_nearest(sc->n, sc->sites, o);
+  /* origin within band of a plane of its cell */
+  for (int64_t q = sc->off[cell]; q < sc->off[cell + 1]; ++q) {
+    if (plane_dist(sc->sites + 3 * cell, sc->sites + 3 * (int64_t)sc->idx[q], o) < p->band_eps)
+      *flags |= VTO_F_NEAR_ORIGIN;
+  }
+  double T = 1.0, t_in = 0.0;
+  int32_t k = 0;
+  for (;;) {
+    if (k >= p->max_steps) {
+      *flags |= VTO_F_MAX_STEPS;
+      break;
+    }
+    ++k;
+    const double* si = sc->sites + 3 * cell;
+    double best_t = INFINITY;
+    int64_t best_j = -1;
+    for (int64_t q = sc->off[cell]; q < sc->off[cell + 1]; ++q) {
+      int64_t j = sc->idx[q];
+      const double* sj = sc->sites + 3 * j;
+      double n[3] = {sj[0] - si[0], sj[1] - si[1], sj[2] - si[2]};
+      double den = dot3(n, d);
+      if (!(den > 0.0)) continue;
+      double mo[3] = {0.5 * (si[0] + sj[0]) - o[0], 0.5 * (si[1] + sj[1]) - o[1],
+                      0.5 * (si[2] + sj[2]) - o[2]};
+      double t = dot3(n, mo) / den;
+      if (t < best_t) { /* strict: exact ties keep the lower CSR position */
+        best_t = t;
+        best_j = j;
+      }
+    }
+    vto_seg s;
+    memset(&s, 0, sizeof(s));
+    s.cell = cell;
+    s.t_in = t_in;
+    s.t_out = best_t;
+    s.next = best_j;
+    s.a = t_in > t0 ? t_in : t0;
+    s.b = best_t < t1 ? best_t : t1;
+    s.T_before = T;
+    /* band: the point where this segment ends is close to another plane */
+    {
+      double te = best_t < t1 ? best_t : t1;
+      if (isfinite(te)) {
+        double xe[3] = {o[0] + te * d[0], o[1] + te * d[1], o[2] + te * d[2]};
+        for (int64_t q = sc->off[cell]; q < sc->off[cell + 1]; ++q) {
+          int64_t j = sc->idx[q];
+          if (j == best_j && best_t < t1) continue;
+          if (plane_dist(si, sc->sites + 3 * j, xe) < p->band_eps) {
+            *flags |= (best_t < t1) ? VTO_F_NEAR_EDGE : VTO_F_NEAR_CLIP;
+          }
+        }
+      }
+      if (isfinite(best_t) && (fabs(best_t - t1) < p->band_eps || fabs(best_t - t0) < p->band_eps))
+        *flags |= VTO_F_NEAR_CLIP;
+    }
+    int stop = 0;
+    if (s.b > s.a) {
+      double delta = s.b - s.a;
+      double sig = sc->sigma[cell];
+      double e = exp(-sig * delta);
+      double alpha = 1.0 - e;
+      double w = T * alpha;
+      s.composited = 1;
+      s.delta = delta;
+      s.alpha = alpha;
+      s.w = w;
+      if (p->skip_weight > 0.0 && fabs(w / p->skip_weight - 1.0) < 1e-4) *flags |= VTO_F_SKIP_AMBIG;
+      if (!(p->skip_weight > 0.0) || w >= p->skip_weight) {
+        s.coloured = 1;
+        cell_colour(sc, cell, taps, tw, s.c);
+        for (int ch = 0; ch < 3; ++ch) C[ch] += w * s.c[ch];
+      }
+      T = T * e;
+      if (fabs(T / p->T_eps - 1.0) < 1e-4) *flags |= VTO_F_T_AMBIG;
+      if (T < p->T_eps) stop = 1;
+    }
+    if (seg_push(segs, &s) != VTO_OK) return VTO_ERR_MEM;
+    *last_next = best_j;
+    *last_t_out = best_t;
+    if (stop || !(best_t < t1) || best_j < 0) break;
+    cell = best_j;
+    t_in = best_t;
+  }
+  for (int ch = 0; ch < 3; ++ch) C[ch] += T * p->bg[ch];
+  *T_out = T;
+  *steps = k;
+  return VTO_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Forward render, threaded over rays.                                  */
+typedef struct {
+  const vto_scene* sc;
+  const vto_params* p;
+  const double *o, *d;
+  double *rgb, *T;
+  int32_t *steps, *flags;
+  int64_t lo, hi;
+  /* optional trace output: per ray up to max_cells cells */
+  int32_t max_cells;
+  int32_t* cells;
+  double* t_out;
+  int32_t* n_cells;
+  int status;
+} render_job;
+
+static void* render_worker(void* arg) {
+  render_job* J = (render_job*)arg;
+  seg_buf b = {0, 0, 0};
+  J->status = VTO_OK;
+  for (int64_t r = J->lo; r < J->hi; ++r) {
+    double C[3], T;
+    int32_t k, fl;
+    int64_t ln;
+    double lt;
+    if (walk_ray(J->sc, J->p, J->o + 3 * r, J->d + 3 * r, &b, C, &T, &k, &fl, &ln, &lt) != VTO_OK) {
+      J->status = VTO_ERR_MEM;
+      break;
+    }
+    if (J->rgb)
+      for (int ch = 0; ch < 3; ++ch) J->rgb[3 * r + ch] = C[ch];
+    if (J->T) J->T[r] = T;
+    if (J->steps) J->steps[r] = k;
+    if (J->flags) J->flags[r] = fl;
+    if (J->cells) {
+      int64_t m = b.n < J->max_cells ? b.n : J->max_cells;
+      for (int64_t q = 0; q < m; ++q) {
+        J->cells[r * J->max_cells + q] = (int32_t)b.s[q].cell;
+        if (J->t_out) J->t_out[r * J->max_cells + q] = b.s[q].t_out;
+      }
+      J->n_cells[r] = (int32_t)b.n;
+    }
+  }
+  free(b.s);
+  return NULL;
+}
+
+static int run_threads(render_job* proto, int64_t n_rays, int n_threads) {
+  if (n_threads < 1) n_threads = 1;
+  if (n_threads > 256) n_threads = 256;
+  if (n_rays < n_threads) n_threads = n_rays > 0 ? (int)n_rays : 1;
+  pthread_t th[256];
+  render_job jobs[256];
+  int64_t chunk = (n_rays + n_threads - 1) / n_threads;
+  int started = 0;
+  for (int t = 0; t < n_threads; ++t) {
+    jobs[t] = *proto;
+    jobs[t].lo = t * chunk;
+    jobs[t].hi = (t + 1) * chunk < n_rays ? (t + 1) * chunk : n_rays;
+    if (jobs[t].lo >= jobs[t].hi) continue;
+    if (n_threads == 1) {
+      render_worker(&jobs[t]);
+      continue;
+    }
+    pthread_create(&th[t], NULL, render_worker, &jobs[t]);
+    started |= 1;
+  }
+  int st = VTO_OK;
+  for (int t = 0; t < n_threads; ++t) {
+    if (jobs[t].lo >= jobs[t].hi) continue;
+    if (n_threads > 1) pthread_join(th[t], NULL);
+    if (jobs[t].status != VTO_OK) st = jobs[t].status;
+  }
+  (void)started;
+  return st;
+}
+
+int vto_render(const vto_scene* sc, int64_t n_rays, const double* o, const double* d,
+               const vto_params* p, double* rgb, double* T, int32_t* steps, int32_t* flags,
+               int n_threads) {
+  render_job J;
+  memset(&J, 0, sizeof(J));
+  J.sc = sc;
+  J.p = p;
+  J.o = o;
+  J.d = d;
+  J.rgb = rgb;
+  J.T = T;
+  J.steps = steps;
+  J.flags = flags;
+  return run_threads(&J, n_rays, n_threads);
+}
+
+/* Per-ray visited cells (walk order) and exit parameters, up to max_cells. */
+int vto_trace(const vto_scene* sc, int64_t n_rays, const double* o, const double* d,
+              const vto_params* p, int32_t max_cells, int32_t* cells, double* t_out,
+              int32_t* n_cells, int32_t* flags, int n_threads) {
+  render_job J;
+  memset(&J, 0, sizeof(J));
+  J.sc = sc;
+  J.p = p;
+  J.o = o;
+  J.d = d;
+  J.flags = flags;
+  J.max_cells = max_cells;
+  J.cells = cells;
+  J.t_out = t_out;
+  J.n_cells = n_cells;
+  return run_threads(&J, n_rays, n_threads);
+}
+
+/* Full segment list of one ray (for pins): arrays of length cap. Returns the
+ * number of walked cells, or -1 on error.                                   */
+int64_t vto_segments(const vto_scene* sc, const double o[3], const double d[3], const vto_params* p,
+                     int64_t cap, int64_t* cell, double* a, double* b, double* delta,
+                     int32_t* composited, double* T_before, double* alpha) {
+  seg_buf sb = {0, 0, 0};
+  double C[3], T;
+  int32_t k, fl;
+  int64_t ln;
+  double lt;
+  if (walk_ray(sc, p, o, d, &sb, C, &T, &k, &fl, &ln, &lt) != VTO_OK) {
+    free(sb.s);
+    return -1;
+  }
+  int64_t m = sb.n < cap ? sb.n : cap;
+  for (int64_t q = 0; q < m; ++q) {
+    cell[q] = sb.s[q].cell;
+    a[q] = sb.s[q].a;
+    b[q] = sb.s[q].b;
+    delta[q] = sb.s[q].delta;
+    composited[q] = sb.s[q].composited;
+    T_before[q] = sb.s[q].T_before;
+    alpha[q] = sb.s[q].alpha;
+  }
+  int64_t n = sb.n;
+  free(sb.s);
+  return n;
+}
+
+/* ------------------------------------------------------------------ */
+/* Backward: gradient of L with respect to sites, densities and texels,
+ * given dL/dC per ray. Single-threaded, accumulates into the outputs (the
+ * caller zeroes them).
+ *
+ * With g = dL/dC, S_k = sum_{m>k} w_m c_m + T_final bg:
+ *   dL/dtau_k   = g.(T_{k+1} c_k - S_k)              (tau_k = sigma delta_k)
+ *   dL/dsigma_k = dL/dtau_k * delta_k                 (matches Eq. 3)
+ *   dL/dc_k     = g * w_k  -> texels by bilinear weight
+ *   crossing b between walked cells k, k+1 at t_b, t_near' < t_b < t_far':
+ *     dL/dt_b = sigma_k dL/dtau_k - sigma_{k+1} dL/dtau_{k+1}
+ *     dt_b/ds_k     = (x_b - s_k) / (n.d)
+ *     dt_b/ds_{k+1} = (s_{k+1} - x_b) / (n.d),  n = s_{k+1} - s_k.
+ * When the walk stopped by transmittance inside (t_near', t_far'), the exit
+ * plane of the last cell still moves delta_K; its far side gets no dtau. */
+int vto_render_bwd(const vto_scene* sc, int64_t n_rays, const double* o, const double* d,
+                   const vto_params* p, const double* grad_rgb, double* g_sites, double* g_sigma,
+                   double* g_tex) {
+  seg_buf sb = {0, 0, 0};
+  double* dtau = NULL;
+  int64_t dcap = 0;
+  int64_t RR = (int64_t)sc->R * sc->R;
+  for (int64_t r = 0; r < n_rays; ++r) {
+    const double* orr = o + 3 * r;
+    const double* drr = d + 3 * r;
+    double C[3], T;
+    int32_t k, fl;
+    int64_t last_next;
+    double last_t;
+    if (walk_ray(sc, p, orr, drr, &sb, C, &T, &k, &fl, &last_next, &last_t) != VTO_OK) {
+      free(sb.s);
+      free(dtau);
+      return VTO_ERR_MEM;
+    }
+    if (fl & VTO_F_BAD_RAY) continue;
+    const double* g = grad_rgb + 3 * r;
+    double t0, t1;
+    clip_extent(p, orr, drr, &t0, &t1);
+    if (!(t1 > t0)) continue;
+    if (sb.n > dcap) {
+      dcap = sb.n * 2;
+      double* nd = (double*)realloc(dtau, (size_t)dcap * sizeof(double));
+      if (!nd) {
+        free(sb.s);
+        free(dtau);
+        return VTO_ERR_MEM;
+      }
+      dtau = nd;
+    }
+    double uv[2];
+    vto_oct(drr, uv);
+    int64_t taps[4];
+    double tw[4];
+    vto_bilinear_taps(sc->R, uv[0], uv[1], taps, tw);
+    /* suffix S_k computed back to front from T_final * bg */
+    double S[3] = {T * p->bg[0], T * p->bg[1], T * p->bg[2]};
+    for (int64_t q = sb.n - 1; q >= 0; --q) {
+      vto_seg* s = &sb.s[q];
+      dtau[q] = 0.0;
+      if (!s->composited) continue;
+      double Tn = s->T_before * (1.0 - s->alpha);
+      double acc = 0.0;
+      for (int ch = 0; ch < 3; ++ch) acc += g[ch] * (Tn * (s->coloured ? s->c[ch] : 0.0) - S[ch]);
+      dtau[q] = acc;
+      if (s->coloured)
+        for (int ch = 0; ch < 3; ++ch) S[ch] += s->w * s->c[ch];
+    }
+    for (int64_t q = 0; q < sb.n; ++q) {
+      vto_seg* s = &sb.s[q];
+      int64_t i = s->cell;
+      if (s->composited) {
+        g_sigma[i] += dtau[q] * s->delta;
+        if (s->coloured)
+          for (int tq = 0; tq < 4; ++tq)
+            for (int ch = 0; ch < 3; ++ch) g_tex[(i * RR + taps[tq]) * 3 + ch] += g[ch] * s->w * tw[tq];
+      }
+      /* crossing at the exit of this cell */
+      int64_t j = s->next;
+      double tb = s->t_out;
+      if (j < 0 || !(tb > t0) || !(tb < t1)) continue;
+      double dt_b = sc->sigma[i] * dtau[q];
+      if (q + 1 < sb.n) dt_b -= sc->sigma[j] * dtau[q + 1];
+      if (dt_b == 0.0) continue;
+      const double* si = sc->sites + 3 * i;
+      const double* sj = sc->sites + 3 * j;
+      double n[3] = {sj[0] - si[0], sj[1] - si[1], sj[2] - si[2]};
+      double nd = dot3(n, drr);
+      double xb[3] = {orr[0] + tb * drr[0], orr[1] + tb * drr[1], orr[2] + tb * drr[2]};
+      for (int c = 0; c < 3; ++c) {
+        g_sites[3 * i + c] += dt_b * (xb[c] - si[c]) / nd;
+        g_sites[3 * j + c] += dt_b * (sj[c] - xb[c]) / nd;
+      }
+    }
+  }
+  free(sb.s);
+  free(dtau);
+  return VTO_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Ray generation (Sec. 6.5: only the rays change between camera models).
+ * Basis: f = fwd/|fwd|, r = (f x up)/|f x up|, u = r x f. Pixel (x, y) with
+ * row 0 at the top, sample point at the pixel centre. Ray order:
+ * [row][col][lens sample]. Directions are unit length.                      */
+typedef struct {
+  int32_t kind; /* 0 pinhole, 1 equidistant fisheye, 2 rolling shutter, 3 thin lens */
+  int32_t w, h;
+  double eye[3], fwd[3], up[3];
+  double fov_y;         /* pinhole-type vertical field of view (radians)   */
+  double fisheye_fov;   /* fisheye field of view across the width (rad)     */
+  double rs_velocity[3];/* rolling shutter: centre moves velocity*time       */
+  double lens_radius, focus_dist;
+  int32_t lens_samples; /* thin lens: square number of stratified samples    */
+  uint64_t seed;
+} vto_camera;
+
+static void normalize3(double v[3]) {
+  double l = sqrt(dot3(v, v));
+  v[0] /= l;
+  v[1] /= l;
+  v[2] /= l;
+}
+static void cross3(const double a[3], const double b[3], double c[3]) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* SplitMix64 (Steele, Lea & Flood, 2014) as a counter-based generator: the
+ * value for counter c under key s is mix(s ^ mix(c)); 24 high bits -> [0,1). */
+uint64_t vto_mix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+double vto_uniform(uint64_t seed, uint64_t counter) {
+  uint64_t h = vto_mix64(seed ^ vto_mix64(counter));
+  return (double)(h >> 40) * (1.0 / 16777216.0);
+}
+
+/* Concentric square-to-disk map (Shirley & Chiu, 1997). */
+void vto_concentric(double a, double b, double out[2]) {
+  if (a == 0.0 && b == 0.0) {
+    out[0] = out[1] = 0.0;
+    return;
+  }
+  double r, phi;
+  if (fabs(a) > fabs(b)) {
+    r = a;
+    phi = (M_PI / 4.0) * (b / a);
+  } else {
+    r = b;
+    phi = M_PI / 2.0 - (M_PI / 4.0) * (a / b);
+  }
+  out[0] = r * cos(phi);
+  out[1] = r * sin(phi);
+}
+
+int64_t vto_camera_rays(const vto_camera* c) {
+  int64_t s = c->kind == 3 ? c->lens_samples : 1;
+  return (int64_t)c->w * c->h * s;
+}
+
+int vto_raygen(const vto_camera* c, double* o, double* d, double* time) {
+  if (c->w <= 0 || c->h <= 0) return VTO_ERR_ARG;
+  double f[3] = {c->fwd[0], c->fwd[1], c->fwd[2]};
+  normalize3(f);
+  double r[3], u[3];
+  cross3(f, c->up, r);
+  normalize3(r);
+  cross3(r, f, u);
+  int32_t S = 1, m = 1;
+  if (c->kind == 3) {
+    S = c->lens_samples;
+    m = (int32_t)floor(sqrt((double)S) + 0.5);
+    if (S <= 0 || m * m != S) return VTO_ERR_ARG;
+  }
+  double ty = tan(0.5 * c->fov_y), tx = ty * (double)c->w / (double)c->h;
+  double fpx = (0.5 * c->w) / (0.5 * c->fisheye_fov);
+  for (int32_t y = 0; y < c->h; ++y)
+    for (int32_t x = 0; x < c->w; ++x)
+      for (int32_t s = 0; s < S; ++s) {
+        int64_t ray = ((int64_t)y * c->w + x) * S + s;
+        double oo[3] = {c->eye[0], c->eye[1], c->eye[2]};
+        double dd[3];
+        double tm = 0.0;
+        if (c->kind == 1) {
+          double px = x + 0.5 - 0.5 * c->w, py = 0.5 * c->h - (y + 0.5);
+          double rr = sqrt(px * px + py * py);
+          double th = rr / fpx;
+          double cp = rr > 0.0 ? px / rr : 1.0, sp = rr > 0.0 ? py / rr : 0.0;
+          double ct = cos(th), st = sin(th);
+          for (int k = 0; k < 3; ++k) dd[k] = ct * f[k] + st * (cp * r[k] + sp * u[k]);
+        } else {
+          double px = (2.0 * (x + 0.5) / c->w - 1.0) * tx;
+          double py = (1.0 - 2.0 * (y + 0.5) / c->h) * ty;
+          double pd[3];
+          for (int k = 0; k < 3; ++k) pd[k] = f[k] + px * r[k] + py * u[k];
+          if (c->kind == 2) {
+            tm = (double)y / (double)c->h;
+            for (int k = 0; k < 3; ++k) oo[k] += tm * c->rs_velocity[k];
+            for (int k = 0; k < 3; ++k) dd[k] = pd[k];
+          } else if (c->kind == 3) {
+            int32_t sx = s % m, sy = s / m;
+            uint64_t pix = (uint64_t)y * c->w + x;
+            double j1 = vto_uniform(c->seed, ((pix * S + s) << 1) | 0u);
+            double j2 = vto_uniform(c->seed, ((pix * S + s) << 1) | 1u);
+            double a = 2.0 * ((sx + j1) / m) - 1.0, b = 2.0 * ((sy + j2) / m) - 1.0;
+            double disk[2];
+            vto_concentric(a, b, disk);
+            for (int k = 0; k < 3; ++k)
+              oo[k] += c->lens_radius * (disk[0] * r[k] + disk[1] * u[k]);
+            /* point on the plane of focus (pd.f == 1, so depth focus_dist) */
+            for (int k = 0; k < 3; ++k) dd[k] = c->eye[k] + c->focus_dist * pd[k] - oo[k];
+          } else {
+            for (int k = 0; k < 3; ++k) dd[k] = pd[k];
+          }
+        }
+        normalize3(dd);
+        for (int k = 0; k < 3; ++k) {
+          o[3 * ray + k] = oo[k];
+          d[3 * ray + k] = dd[k];
+        }
+        if (time) time[ray] = tm;
+      }
+  return VTO_OK;
+}
