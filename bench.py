@@ -1,0 +1,423 @@
+"""Benchmark: Mrays/s of the differentiable Voronoi ray-traversal renderer.
+
+One step = one pass of the whole hot path over one batch of views: ray
+generation -> start-cell search -> forward walk/composite -> L2 loss ->
+backward re-traversal with gradient atomics (sites, sigma, texels).
+
+Default workload "prec3m": 3,000,000 surface-concentrated sites with 8x8
+octahedral textures, four 1280x832 pinhole cameras (4,259,840 rays), textures
+stored in FP16 (the headline) and also timed in FP32 and BF16. Inputs are
+synthetic and seeded (the paper's Mip-NeRF 360 scenes are not available).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch under torch.distributed.run; each rank renders its own
+views of the same scene (weak scaling, no collective in the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2608_17682_gb300 import workloads as W  # noqa: E402
+
+METRIC = "Mrays/s fwd+bwd (FP16 textures)"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="prec3m", choices=list(W.WORKLOADS))
+    ap.add_argument("--sites", type=int, default=0, help="override the site count (smaller runs)")
+    ap.add_argument("--tex", default="f16", choices=["f16", "f32", "bf16"])
+    ap.add_argument("--no-extra", action="store_true", help="skip the FP32/BF16 comparison timings")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def rank_cameras(wl, rank):
+    """Weak scaling: rank r renders the workload's views rotated by r*7.5 deg."""
+    if rank == 0:
+        return wl.cameras
+    cams = []
+    for c in wl.cameras:
+        eye = np.asarray(c.eye)
+        a = math.radians(7.5 * rank)
+        R = np.array([[math.cos(a), -math.sin(a), 0], [math.sin(a), math.cos(a), 0], [0, 0, 1]])
+        e2 = R @ eye
+        f2 = R @ np.asarray(c.fwd)
+        cams.append(W.Camera(**{**c.__dict__, "eye": tuple(e2), "fwd": tuple(f2)}))
+    return cams
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if len(r) > 5 + k and r[5 + k] == "Active"})
+        pw = [float(r[3]) for r in self.rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows), "power_w_max": max(pw) if pw else None}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": HBM_FALLBACK_GBS}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2608_17682_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_2608_17682_gb300", "csrc", f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)
+    except OSError:
+        return None
+    e = rec.get(f"{kernel}:{workload}")
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args, ws, rank, local):
+    import torch
+
+    from paper_2608_17682_gb300 import api
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    wl = W.make_workload(args.workload, n_sites=args.sites or None)
+    cams = rank_cameras(wl, rank)
+    n_img = len(cams)
+    c0 = cams[0]
+    spp = c0.lens_samples if c0.kind == 3 else 1
+    n_rays = sum(c.n_rays for c in cams)
+    uniform = all(c.w == c0.w and c.h == c0.h and c.n_rays == c0.n_rays for c in cams)
+    params = api.make_params(**wl.params, **(dict(img_w=c0.w * spp, img_h=c0.h, n_images=n_img) if uniform else {}))
+    Y = torch.as_tensor(W.target_image(n_rays, wl.seed), device=dev)
+
+    scenes = {}
+    dtypes = [args.tex] + ([] if args.no_extra else [t for t in ("f32", "bf16", "f16") if t != args.tex])
+    for t in dtypes:
+        scenes[t] = api.Scene.from_workload(wl.scene, tex_dtype=t, device=dev)
+    stream = torch.cuda.current_stream()
+    o = torch.empty(n_rays, 3, device=dev)
+    d = torch.empty(n_rays, 3, device=dev)
+    tm = torch.empty(n_rays, device=dev)
+    rgb = torch.empty(n_rays, 3, device=dev)
+    T = torch.empty(n_rays, device=dev)
+    steps = torch.empty(n_rays, dtype=torch.int32, device=dev)
+    N, R = wl.scene.n, wl.scene.R
+    gs = torch.empty(N, 3, device=dev)
+    gsig = torch.empty(N, device=dev)
+    gt = torch.empty(N, R, R, 3, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)  # 256 MB > 129 MB L2
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(scene, marks=None, fwd_only=False):
+        api.generate_rays(cams, out=(o, d, tm))
+        if marks:
+            marks[0].record(stream)
+        api.render_fwd(scene, o, d, params, time=tm, out=(rgb, T, steps))
+        if marks:
+            marks[1].record(stream)
+        if fwd_only:
+            return
+        loss, grad = api.l2_loss(rgb, Y)
+        if marks:
+            marks[2].record(stream)
+        api.render_bwd(scene, o, d, params, rgb, grad, time=tm, out=(gs, gsig, gt))
+        if marks:
+            marks[3].record(stream)
+        return loss
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def timed(scene, K, fwd_only=False):
+        """K steps, L2 flushed between steps (outside the timed events)."""
+        for _ in range(args.warmup):
+            step(scene, fwd_only=fwd_only)
+        barrier()
+        st, en, marks = [], [], []
+        for _ in range(K):
+            flush.zero_()
+            a, b = ev(), ev()
+            m = [ev() for _ in range(4)]
+            a.record(stream)
+            step(scene, m, fwd_only=fwd_only)
+            b.record(stream)
+            st.append(a)
+            en.append(b)
+            marks.append(m)
+        barrier()
+        total = sum(x.elapsed_time(y) for x, y in zip(st, en))
+        fwd = sum(m[0].elapsed_time(m[1]) for m in marks) / K
+        bwd = 0.0 if fwd_only else sum(m[2].elapsed_time(m[3]) for m in marks) / K
+        return total / K, fwd, bwd
+
+    main = scenes[args.tex]
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_step, ms_fwd, ms_bwd = timed(main, args.steps)
+    clk = clocks.stop()
+    # the max over ranks
+    if ws > 1:
+        t = torch.tensor([ms_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = t.item()
+    err, fp64 = main.get_error()
+    if err:
+        raise RuntimeError(f"kernel error {err}")
+    sum_steps = int(steps.long().sum().item())
+    total_rays = n_rays * ws
+    value = total_rays / (ms_step * 1e-3) / 1e6
+
+    # forward-only and other texture precisions (context keys)
+    extra = {}
+    ms_f, fwd_only_fwd, _ = timed(main, max(3, args.steps // 2), fwd_only=True)
+    extra["fwd_only_mrays_s"] = round(n_rays / (ms_f * 1e-3) / 1e6 * ws, 2)
+    for t in dtypes[1:]:
+        m_s, m_f, m_b = timed(scenes[t], max(3, args.steps // 2))
+        extra[t] = {"fwd_bwd_mrays_s": round(n_rays / (m_s * 1e-3) / 1e6 * ws, 2), "ms_fwd": round(m_f, 3),
+                    "ms_bwd": round(m_b, 3)}
+
+    # end to end through the public API with host buffers: H2D target image,
+    # D2H rendered image + loss, inside the timed region
+    Yh = torch.as_tensor(W.target_image(n_rays, wl.seed)).pin_memory()
+    rgb_h = torch.empty(n_rays, 3).pin_memory()
+    loss_h = torch.empty(1).pin_memory()
+    Yd = torch.empty_like(Y)
+
+    def e2e_step():
+        Yd.copy_(Yh, non_blocking=True)
+        api.generate_rays(cams, out=(o, d, tm))
+        api.render_fwd(main, o, d, params, time=tm, out=(rgb, T, steps))
+        loss, grad = api.l2_loss(rgb, Yd)
+        api.render_bwd(main, o, d, params, rgb, grad, time=tm, out=(gs, gsig, gt))
+        rgb_h.copy_(rgb, non_blocking=True)
+        loss_h.copy_(loss, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    barrier()
+    a, b = ev(), ev()
+    a.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    b.record(stream)
+    barrier()
+    ms_e2e = a.elapsed_time(b) / args.steps
+    e2e = {"value": round(total_rays / (ms_e2e * 1e-3) / 1e6, 3), "unit": "Mrays/s",
+           "h2d_bytes_per_step": int(Yh.numel() * 4), "d2h_bytes_per_step": int(rgb_h.numel() * 4 + 4)}
+
+    # roofline of the dominant kernel (algorithmic bytes per visited cell)
+    peaks, peak_kind = measured_peaks()
+    E = main.n_edges
+    tb = 8 if args.tex in ("f16", "bf16") else 16
+    b_fwd_step = 16 + 16 * E / N + 4 * tb  # meta + neighbour records + 4 texels
+    b_bwd_step = b_fwd_step + 2 * (16 + 4 * 16)  # + RMW of one cell and four texel gradient float4s
+    io_fwd, io_bwd = 24 + 20, 24 + 24
+    dom = "bwd" if ms_bwd >= ms_fwd else "fwd"
+    ms_dom = ms_bwd if dom == "bwd" else ms_fwd
+    alg = sum_steps * (b_bwd_step if dom == "bwd" else b_fwd_step) + n_rays * (io_bwd if dom == "bwd" else io_fwd)
+    achieved = alg / (ms_dom * 1e-3) / 1e9
+    peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+    kname = "k_walk<BWD>" if dom == "bwd" else "k_walk<FWD>"
+    roof = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": recorded_traffic(kname, args.workload),
+            "algorithmic_bytes_per_launch": int(alg), "peak_source": f"{peak_kind} hbm_gbs",
+            "ms_per_launch": round(ms_dom, 4)}
+
+    line = {
+        "metric": METRIC if args.tex == "f16" else METRIC.replace("FP16", args.tex.upper()),
+        "value": round(value * 1.0, 3), "unit": "Mrays/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {N} sites, {R}x{R} {args.tex} textures, "
+                               f"{n_img} x {c0.w}x{c0.h} cameras, {n_rays} rays/GPU",
+                   "global_batch": total_rays, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": "flushed between timed steps (256 MB write outside the timed events)",
+                   "scene_bytes": int(N * 32 + E * 16 + N * R * R * tb)},
+        "ms_fwd": round(ms_fwd, 4), "ms_bwd": round(ms_bwd, 4),
+        "fps_fwd_bwd": round(n_img / (ms_step * 1e-3), 2),
+        "mean_cells_per_ray": round(sum_steps / n_rays, 3), "fp64_rechecks_per_step": fp64 / max(1, args.steps + args.warmup),
+        "clocks": clk, "e2e": e2e, "gpu_launches": 9 * args.steps, "roofline": roof, **extra,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(wl, cams, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------- oracle arm
+
+def oracle_sample_rays(cams, n):
+    """A fixed strided sample of n rays of the views, generated by the oracle."""
+    import oracle as O
+
+    per = [c.n_rays for c in cams]
+    total = sum(per)
+    stride = max(1, total // n)
+    pick = np.arange(0, total, stride)[:n]
+    os_, ds = [], []
+    base = 0
+    for c, m in zip(cams, per):
+        sel = pick[(pick >= base) & (pick < base + m)] - base
+        if len(sel):
+            o, d, _ = O.raygen(c)
+            os_.append(o[sel].astype(np.float32))
+            ds.append(d[sel].astype(np.float32))
+        base += m
+    return np.concatenate(os_), np.concatenate(ds)
+
+
+def oracle_step(osc, o, d, Y, params):
+    import oracle as O
+
+    rgb, T, steps, flags = O.render(osc, o, d, params=params)
+    g = 2 * (rgb - Y) / (3 * len(o))
+    O.render_bwd(osc, o, d, g, params=params)
+
+
+def cpu_baseline(wl, cams, seconds):
+    import oracle as O
+
+    osc = O.OracleScene.from_workload_scene(wl.scene)
+    params = O.make_params(**wl.params)
+    n = 64
+    while True:
+        o, d = oracle_sample_rays(cams, n)
+        Y = W.target_image(len(o), wl.seed)
+        t = time.time()
+        oracle_step(osc, o, d, Y, params)
+        dt = time.time() - t
+        if dt * 4 > seconds or n >= 1 << 20:
+            break
+        n *= 4
+    rate = len(o) / dt / 1e6
+    return {"value": round(rate, 6), "unit": "Mrays/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{len(o)} rays strided over the views, fwd (threaded) + bwd (threaded walk, serial "
+                      f"accumulation), FP64, {dt:.1f} s"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle as O
+
+    wl = W.make_workload(args.workload, n_sites=args.sites or None)
+    osc = O.OracleScene.from_workload_scene(wl.scene)
+    params = O.make_params(**wl.params)
+    n = 256
+    o, d = oracle_sample_rays(wl.cameras, n)
+    Y = W.target_image(len(o), wl.seed)
+    for _ in range(args.warmup):
+        oracle_step(osc, o, d, Y, params)
+    t = time.time()
+    for _ in range(args.steps):
+        oracle_step(osc, o, d, Y, params)
+    dt = (time.time() - t) / args.steps
+    v = len(o) / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": "Mrays/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {wl.scene.n} sites (oracle on a {len(o)}-ray sample per step)"},
+            "cpu_baseline": {"value": round(v, 6), "unit": "Mrays/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{len(o)} rays strided over the views per step"},
+            "e2e": {"value": round(v, 6), "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,234 @@
+/*
+ * vt.h -- C ABI of libvt.so: differentiable volume rendering by ray traversal
+ * of a 3D Voronoi diagram, hand-written CUDA for sm_103a (GB300).
+ *
+ * Method (arXiv 2608.17682, "Differentiable Voronoi Ray Tracing Beyond
+ * Rasterization Speeds"):
+ *   - Sec. 3.1: a ray starts in the Voronoi cell containing its origin (one
+ *     nearest-site query) and walks from cell to cell through the nearest
+ *     forward bisector-plane crossing with the cell's Delaunay neighbours:
+ *       t_j = n.((s_i+s_j)/2 - o) / (n.d),  n = s_j - s_i,  over n.d > 0.
+ *   - Sec. 3.2: piecewise-constant volume rendering, alpha_k = 1 -
+ *     exp(-sigma_{i_k} delta_k), C = sum_k T_k alpha_k c_k, front to back,
+ *     early termination once T falls below a threshold.
+ *   - Sec. 5.1: per-cell R x R RGB octahedral texture, bilinear fetch. This
+ *     library indexes it at the ray direction d.
+ *   - Sec. 5.6: RGB texels padded to RGBA for one aligned load, half-precision
+ *     appearance storage, Morton-ordered cells, warp-coherent 4x8 ray tiles,
+ *     optional low-contribution cell skip.
+ *   - Eq. 3: dL/dsigma = dL/dalpha * delta * (1 - alpha) (the backward pass
+ *     computes the same quantity as dL/dtau * delta, tau = sigma*delta).
+ *   - Sec. 6.5: camera effects by ray generation only.
+ *
+ * Conventions for every entry point:
+ *   - Pointers marked "device" are caller-owned CUDA device pointers (for
+ *     example torch tensors' data_ptr()); "host" pointers are ordinary CPU
+ *     memory. Nothing is retained past the call unless stated.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). All work is enqueued on it; calls return after enqueueing.
+ *   - Errors are returned as vt_status; nothing throws across the ABI.
+ *     Asynchronous faults of earlier work surface as VT_ERR_CUDA. Errors that
+ *     kernels detect (step cap, trace capacity) are recorded on the scene and
+ *     read with vt_scene_get_error().
+ *   - Arrays are C-contiguous, FP32 unless stated; [N,3] means N rows of 3.
+ *   - A scene owns its own reordered device copies; inputs given to
+ *     vt_scene_create/vt_scene_update may be freed after the call returns
+ *     and the stream has been synchronised.
+ */
+#ifndef VT_H
+#define VT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VT_OK = 0,
+  VT_ERR_INVALID_ARG = 1, /* bad size, null pointer, malformed CSR, NaN site ...   */
+  VT_ERR_CUDA = 2,        /* a CUDA runtime call failed (incl. earlier async faults) */
+  VT_ERR_OOM = 3,         /* device allocation failed                               */
+  VT_ERR_MAX_STEPS = 4,   /* a ray walked more than max_steps cells (it was stopped) */
+  VT_ERR_CAPACITY = 5,    /* a trace buffer was too small (output truncated)         */
+  VT_ERR_UNSUPPORTED = 6  /* feature not available in this build                     */
+} vt_status;
+
+/* Storage precision of the octahedral textures (Sec. 5.6 "half-precision
+ * appearance attributes"); compositing and accumulation are always FP32.
+ * FP16 and BF16 are rounded to nearest-even from the FP32 input. */
+typedef enum { VT_F32 = 0, VT_F16 = 1, VT_BF16 = 2 } vt_dtype;
+
+typedef struct vt_scene vt_scene; /* opaque, owned by the library */
+
+/* Scene description (Sec. 3.1 sites and Delaunay graph, Sec. 3.2 densities,
+ * Sec. 5.1 textures). All pointers are DEVICE pointers, user index order. */
+typedef struct {
+  int64_t n_sites;             /* N >= 1                                          */
+  int32_t tex_res;             /* R >= 2: textures are R x R                      */
+  int32_t tex_dtype;           /* vt_dtype of the internal texture copy           */
+  const float* sites;          /* [N,3] site positions p_i, finite                */
+  const float* sigma;          /* [N] densities sigma_i >= 0, finite              */
+  const float* tex;            /* [N,R,R,3] RGB, row y then column x (see below)  */
+  const int64_t* adj_offsets;  /* [N+1] CSR row offsets, adj_offsets[0] == 0     */
+  const int32_t* adj_indices;  /* [E] neighbour ids; symmetric, no self loops,
+                                  no duplicates within a row, E < 2^31; may be
+                                  NULL when E == 0                                 */
+} vt_scene_desc;
+
+/* Render parameters. Rays are r(t) = o + t d for t in [t_near, t_far],
+ * optionally clipped to the box [clip_lo, clip_hi]. */
+typedef struct {
+  float t_near, t_far;     /* ray extent (in units of |d|); default 0, 20              */
+  int32_t use_clip_box;    /* nonzero: also clip to the axis-aligned box               */
+  float clip_lo[3], clip_hi[3];
+  float T_eps;             /* early termination once T < T_eps (after compositing
+                              that cell); 1e-4                                         */
+  float skip_weight;       /* Sec. 5.6: if T*alpha < skip_weight the cell's colour is
+                              not fetched (T still updated). 0 = exact                 */
+  float bg[3];             /* background colour added as T_final * bg                  */
+  int32_t img_w, img_h;    /* ray layout [n_images][img_h][img_w] -> 4x8 warp tiles;
+                              0 = plain 1-D order                                      */
+  int32_t n_images;        /* number of images when img_w > 0                          */
+  int32_t max_steps;       /* cells a ray may visit (<= 0: min(4N, 2^20)); exceeding it
+                              stops the ray and records VT_ERR_MAX_STEPS               */
+} vt_render_params;
+
+/* Fill `p` with the defaults listed above. */
+void vt_render_params_default(vt_render_params* p);
+
+/* Build a scene (Sec. 5.6 one-time preprocessing, untimed in the paper):
+ * validates the inputs (finite sites, sigma >= 0, CSR in range, symmetric,
+ * no self loops, R >= 2), sorts cells by 63-bit Morton code over the sites'
+ * bounding box (ties by user id), permutes sites / densities / textures,
+ * remaps the adjacency and stores each neighbour's position inline with its
+ * CSR entry, pads texels RGB -> RGBA in the requested storage dtype.
+ * On success *out receives a new scene; on error *out is NULL. Synchronises
+ * `stream` before returning (validation result is read on the host). */
+vt_status vt_scene_create(const vt_scene_desc* desc, void* stream, vt_scene** out);
+
+/* Replace sites, densities and textures (device pointers, user order, same
+ * N, R and adjacency as at creation; any may be NULL to keep the old one).
+ * The Morton order of creation is kept. Validates like vt_scene_create. */
+vt_status vt_scene_update(vt_scene* s, const float* sites, const float* sigma, const float* tex,
+                          void* stream);
+
+/* Free a scene. NULL is ignored. Synchronises the device first. */
+void vt_scene_destroy(vt_scene* s);
+
+/* Scene facts: n_sites, tex_res, tex_dtype, number of CSR entries. */
+vt_status vt_scene_info(const vt_scene* s, int64_t* n_sites, int32_t* tex_res, int32_t* tex_dtype,
+                        int64_t* n_edges);
+
+/* Synchronise `stream`, return the first kernel-detected error recorded on the
+ * scene since the last call (VT_ERR_MAX_STEPS, VT_ERR_CAPACITY) or VT_OK,
+ * and clear it. Also returns VT_ERR_CUDA for an asynchronous CUDA fault.
+ * If n_fp64 is not NULL it receives the number of FP64 plane rechecks done
+ * since the last call (grazing planes with |n.d| < 1e-6 |n| |d|). */
+vt_status vt_scene_get_error(vt_scene* s, void* stream, int64_t* n_fp64);
+
+/* ---------------------------------------------------------------------- */
+/* Cameras (Sec. 6.5 / application appendix: only ray generation changes).
+ * Basis: f = fwd/|fwd|, r = (f x up)/|f x up|, u = r x f. Pixel (x,y), row 0
+ * at the top, rays through pixel centres. Rays are written in the order
+ * [camera][row][col][lens sample]; directions are unit length.
+ *   PINHOLE:          d ~ f + px r + py u, px = (2(x+.5)/w - 1) tan(fov_y/2) w/h,
+ *                     py = (1 - 2(y+.5)/h) tan(fov_y/2).
+ *   FISHEYE_EQUIDIST: angle to f = rho / F, rho = pixel-centre distance from the
+ *                     image centre in pixels, F = (w/2)/(fisheye_fov/2);
+ *                     azimuth = atan2(py, px) in the (r, u) plane.
+ *   ROLLING_SHUTTER:  pinhole directions; row y has time y/h and origin
+ *                     eye + (y/h) * rs_velocity (linear motion per frame).
+ *   THIN_LENS:        lens_samples = m*m stratified samples per pixel; sample s
+ *                     = (sy*m + sx) is jittered in its stratum by a SplitMix64
+ *                     counter hash of (seed, pixel, s), mapped to the disk by
+ *                     Shirley-Chiu's concentric map, origin eye + lens_radius
+ *                     (lx r + ly u); the ray aims at the pinhole ray's point at
+ *                     depth focus_dist along f.
+ * `time` is 0 except for rolling shutter. */
+typedef enum {
+  VT_CAM_PINHOLE = 0,
+  VT_CAM_FISHEYE_EQUIDIST = 1,
+  VT_CAM_ROLLING_SHUTTER = 2,
+  VT_CAM_THIN_LENS = 3
+} vt_cam_kind;
+
+typedef struct {
+  int32_t kind; /* vt_cam_kind */
+  int32_t w, h;
+  float eye[3], fwd[3], up[3];
+  float fov_y;          /* radians                                   */
+  float fisheye_fov;    /* radians across the width (pi = 180 deg)   */
+  float rs_velocity[3]; /* world units per frame                     */
+  float lens_radius, focus_dist;
+  int32_t lens_samples; /* thin lens: a square number >= 1           */
+  uint64_t seed;
+} vt_camera;
+
+/* Number of rays camera `c` produces (w*h, times lens_samples for thin lens). */
+int64_t vt_camera_n_rays(const vt_camera* c);
+
+/* Generate rays for n_cams cameras (HOST array of descriptions) into DEVICE
+ * buffers o [R,3], d [R,3], time [R] (time may be NULL), R = sum of
+ * vt_camera_n_rays. */
+vt_status vt_generate_rays(const vt_camera* cams, int32_t n_cams, float* o, float* d, float* time,
+                           void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Forward render (Sec. 3.1 walk + Sec. 3.2 compositing + Sec. 5.1 colour).
+ *   o, d   : DEVICE [n_rays,3] ray origins and directions (|d| > 0; t is in
+ *            units of |d|; the colour uses d's direction).
+ *   time   : DEVICE [n_rays] or NULL; accepted and ignored (static scene).
+ *   rgb_out: DEVICE [n_rays,3] C = sum_k T_k alpha_k c_k + T_final bg.
+ *   T_out  : DEVICE [n_rays] final transmittance (NULL allowed).
+ *   steps_out: DEVICE [n_rays] int32 cells visited by the walk (NULL allowed).
+ * The start cell of each ray is found by an exact nearest-site search for one
+ * anchor origin per image (per 4096 rays in 1-D layout) followed by a greedy
+ * walk over the Delaunay graph to the ray's own origin. */
+vt_status vt_render_fwd(vt_scene* s, int64_t n_rays, const float* o, const float* d, const float* time,
+                        const vt_render_params* p, float* rgb_out, float* T_out, int32_t* steps_out,
+                        void* stream);
+
+/* Backward render: re-traverses every ray with decisions identical to
+ * vt_render_fwd (no per-ray cell lists are stored) and accumulates
+ *   grad_sites [N,3] (through the bisector-plane crossings),
+ *   grad_sigma [N]   (dL/dtau * delta, Eq. 3),
+ *   grad_tex   [N,R,R,3] (bilinear weights * T alpha * dL/dC),
+ * all DEVICE FP32 in USER index order, OVERWRITTEN (the call zero-fills them).
+ * rgb_out is the forward's output for the same rays and parameters;
+ * grad_rgb is dL/dC [n_rays,3]. Any of the three gradient pointers may be
+ * NULL to skip that output. Library-owned scratch (one float4 per cell and
+ * per texel) is allocated on first use and kept with the scene. */
+vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float* d, const float* time,
+                        const vt_render_params* p, const float* rgb_out, const float* grad_rgb,
+                        float* grad_sites, float* grad_sigma, float* grad_tex, void* stream);
+
+/* Debug / parity: visited cells of each ray (walk order, USER ids) and the
+ * exit parameter of each visited cell (+inf if unbounded), up to max_cells
+ * per ray: cells [n_rays,max_cells] int32, t_exit [n_rays,max_cells] (NULL
+ * allowed), n_cells [n_rays] = true count. Overflow records VT_ERR_CAPACITY. */
+vt_status vt_trace_cells(vt_scene* s, int64_t n_rays, const float* o, const float* d,
+                         const vt_render_params* p, int32_t max_cells, int32_t* cells, float* t_exit,
+                         int32_t* n_cells, void* stream);
+
+/* L2 photometric loss of the benchmark workloads: L = mean((C - Y)^2) over
+ * n*3 values; grad = dL/dC = 2 (C - Y) / (3 n). DEVICE pointers; loss_out is
+ * one float (overwritten). */
+vt_status vt_l2_loss(int64_t n, const float* rgb, const float* target, float* grad_out, float* loss_out,
+                     void* stream);
+
+/* Pixel = mean of spp consecutive rays (depth of field, Sec. 6.5):
+ * out [n_pixels,3] from rays [n_pixels*spp,3]; the backward spreads
+ * grad_px / spp to every sample. DEVICE pointers. */
+vt_status vt_average_samples(int64_t n_pixels, int32_t spp, const float* rgb_rays, float* rgb_px,
+                             void* stream);
+vt_status vt_average_samples_bwd(int64_t n_pixels, int32_t spp, const float* grad_px, float* grad_rays,
+                                 void* stream);
+
+/* Human-readable status name (static string). */
+const char* vt_status_str(vt_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VT_H */

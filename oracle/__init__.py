@@ -69,7 +69,7 @@ def lib():
         L.vto_segments.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64] + [C.c_void_p] * 7
         L.vto_segments.restype = C.c_int64
         L.vto_render_bwd.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                                     C.c_void_p, C.c_void_p, C.c_void_p]
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
         L.vto_raygen.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.vto_camera_rays.argtypes = [C.c_void_p]
         L.vto_camera_rays.restype = C.c_int64
@@ -166,7 +166,7 @@ def segments(sc: OracleScene, o, d, cap=4096, params=None, **kw):
     return {k: v[:m] for k, v in out.items()}
 
 
-def render_bwd(sc: OracleScene, o, d, grad_rgb, params=None, **kw):
+def render_bwd(sc: OracleScene, o, d, grad_rgb, params=None, n_threads=0, **kw):
     """FP64 gradients (sites [N,3], sigma [N], tex [N,R,R,3]) for dL/dC."""
     p = params if params is not None else make_params(**kw)
     o, d, g = _f64(o).reshape(-1, 3), _f64(d).reshape(-1, 3), _f64(grad_rgb).reshape(-1, 3)
@@ -174,7 +174,7 @@ def render_bwd(sc: OracleScene, o, d, grad_rgb, params=None, **kw):
     gsig = np.zeros(sc.n)
     gt = np.zeros(sc.tex.shape)
     st = lib().vto_render_bwd(C.byref(sc._s), len(o), _ptr(o), _ptr(d), C.byref(p), _ptr(g), _ptr(gs), _ptr(gsig),
-                              _ptr(gt))
+                              _ptr(gt), _threads(n_threads))
     if st:
         raise RuntimeError(f"oracle bwd failed: {st}")
     return gs, gsig, gt

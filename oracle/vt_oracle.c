@@ -465,42 +465,83 @@ int64_t vto_segments(const vto_scene* sc, const double o[3], const double d[3], 
   return n;
 }
 
-/* ------------------------------------------------------------------ */
-/* Backward: gradient of L with respect to sites, densities and texels,
- * given dL/dC per ray. Single-threaded, accumulates into the outputs (the
- * caller zeroes them).
- *
- * With g = dL/dC, S_k = sum_{m>k} w_m c_m + T_final bg:
- *   dL/dtau_k   = g.(T_{k+1} c_k - S_k)              (tau_k = sigma delta_k)
- *   dL/dsigma_k = dL/dtau_k * delta_k                 (matches Eq. 3)
- *   dL/dc_k     = g * w_k  -> texels by bilinear weight
- *   crossing b between walked cells k, k+1 at t_b, t_near' < t_b < t_far':
- *     dL/dt_b = sigma_k dL/dtau_k - sigma_{k+1} dL/dtau_{k+1}
- *     dt_b/ds_k     = (x_b - s_k) / (n.d)
- *     dt_b/ds_{k+1} = (s_{k+1} - x_b) / (n.d),  n = s_{k+1} - s_k.
- * When the walk stopped by transmittance inside (t_near', t_far'), the exit
- * plane of the last cell still moves delta_K; its far side gets no dtau. */
-int vto_render_bwd(const vto_scene* sc, int64_t n_rays, const double* o, const double* d,
-                   const vto_params* p, const double* grad_rgb, double* g_sites, double* g_sigma,
-                   double* g_tex) {
+/* Gradient contributions are produced per thread as (flat index, value)
+ * pairs -- flat index: [0,3N) sites, [3N,4N) sigma, then texels -- and added
+ * into the outputs under a mutex. */
+typedef struct {
+  int64_t i;
+  double v;
+} contrib;
+
+typedef struct {
+  contrib* c;
+  int64_t n, cap;
+} contrib_buf;
+
+typedef struct {
+  const vto_scene* sc;
+  const vto_params* p;
+  const double *o, *d, *g;
+  double *g_sites, *g_sigma, *g_tex;
+  int64_t lo, hi;
+  pthread_mutex_t* mu;
+  int status;
+} bwd_job;
+
+static int emit(contrib_buf* b, int64_t i, double v) {
+  if (v == 0.0) return VTO_OK;
+  if (b->n == b->cap) {
+    int64_t nc = b->cap ? 2 * b->cap : 4096;
+    contrib* nb = (contrib*)realloc(b->c, (size_t)nc * sizeof(contrib));
+    if (!nb) return VTO_ERR_MEM;
+    b->c = nb;
+    b->cap = nc;
+  }
+  b->c[b->n].i = i;
+  b->c[b->n].v = v;
+  b->n++;
+  return VTO_OK;
+}
+
+static void flush_contribs(bwd_job* J, contrib_buf* b) {
+  int64_t n3 = 3 * J->sc->n, n4 = 4 * J->sc->n;
+  pthread_mutex_lock(J->mu);
+  for (int64_t k = 0; k < b->n; ++k) {
+    int64_t i = b->c[k].i;
+    if (i < n3)
+      J->g_sites[i] += b->c[k].v;
+    else if (i < n4)
+      J->g_sigma[i - n3] += b->c[k].v;
+    else
+      J->g_tex[i - n4] += b->c[k].v;
+  }
+  pthread_mutex_unlock(J->mu);
+  b->n = 0;
+}
+
+static void* bwd_worker(void* arg) {
+  bwd_job* J = (bwd_job*)arg;
+  const vto_scene* sc = J->sc;
+  const vto_params* p = J->p;
   seg_buf sb = {0, 0, 0};
+  contrib_buf cb = {0, 0, 0};
   double* dtau = NULL;
   int64_t dcap = 0;
-  int64_t RR = (int64_t)sc->R * sc->R;
-  for (int64_t r = 0; r < n_rays; ++r) {
-    const double* orr = o + 3 * r;
-    const double* drr = d + 3 * r;
+  const int64_t RR = (int64_t)sc->R * sc->R, n3 = 3 * sc->n, n4 = 4 * sc->n;
+  J->status = VTO_OK;
+  for (int64_t r = J->lo; r < J->hi && J->status == VTO_OK; ++r) {
+    const double* orr = J->o + 3 * r;
+    const double* drr = J->d + 3 * r;
     double C[3], T;
     int32_t k, fl;
     int64_t last_next;
     double last_t;
     if (walk_ray(sc, p, orr, drr, &sb, C, &T, &k, &fl, &last_next, &last_t) != VTO_OK) {
-      free(sb.s);
-      free(dtau);
-      return VTO_ERR_MEM;
+      J->status = VTO_ERR_MEM;
+      break;
     }
     if (fl & VTO_F_BAD_RAY) continue;
-    const double* g = grad_rgb + 3 * r;
+    const double* g = J->g + 3 * r;
     double t0, t1;
     clip_extent(p, orr, drr, &t0, &t1);
     if (!(t1 > t0)) continue;
@@ -508,9 +549,8 @@ int vto_render_bwd(const vto_scene* sc, int64_t n_rays, const double* o, const d
       dcap = sb.n * 2;
       double* nd = (double*)realloc(dtau, (size_t)dcap * sizeof(double));
       if (!nd) {
-        free(sb.s);
-        free(dtau);
-        return VTO_ERR_MEM;
+        J->status = VTO_ERR_MEM;
+        break;
       }
       dtau = nd;
     }
@@ -532,14 +572,15 @@ int vto_render_bwd(const vto_scene* sc, int64_t n_rays, const double* o, const d
       if (s->coloured)
         for (int ch = 0; ch < 3; ++ch) S[ch] += s->w * s->c[ch];
     }
-    for (int64_t q = 0; q < sb.n; ++q) {
+    int st = VTO_OK;
+    for (int64_t q = 0; q < sb.n && st == VTO_OK; ++q) {
       vto_seg* s = &sb.s[q];
       int64_t i = s->cell;
       if (s->composited) {
-        g_sigma[i] += dtau[q] * s->delta;
+        st |= emit(&cb, n3 + i, dtau[q] * s->delta);
         if (s->coloured)
           for (int tq = 0; tq < 4; ++tq)
-            for (int ch = 0; ch < 3; ++ch) g_tex[(i * RR + taps[tq]) * 3 + ch] += g[ch] * s->w * tw[tq];
+            for (int ch = 0; ch < 3; ++ch) st |= emit(&cb, n4 + (i * RR + taps[tq]) * 3 + ch, g[ch] * s->w * tw[tq]);
       }
       /* crossing at the exit of this cell */
       int64_t j = s->next;
@@ -554,14 +595,72 @@ int vto_render_bwd(const vto_scene* sc, int64_t n_rays, const double* o, const d
       double nd = dot3(n, drr);
       double xb[3] = {orr[0] + tb * drr[0], orr[1] + tb * drr[1], orr[2] + tb * drr[2]};
       for (int c = 0; c < 3; ++c) {
-        g_sites[3 * i + c] += dt_b * (xb[c] - si[c]) / nd;
-        g_sites[3 * j + c] += dt_b * (sj[c] - xb[c]) / nd;
+        st |= emit(&cb, 3 * i + c, dt_b * (xb[c] - si[c]) / nd);
+        st |= emit(&cb, 3 * j + c, dt_b * (sj[c] - xb[c]) / nd);
       }
     }
+    if (st != VTO_OK) J->status = VTO_ERR_MEM;
+    if (cb.n > (1 << 20)) flush_contribs(J, &cb);
   }
+  flush_contribs(J, &cb);
+  free(cb.c);
   free(sb.s);
   free(dtau);
-  return VTO_OK;
+  return NULL;
+}
+
+/* ------------------------------------------------------------------ */
+/* Backward: gradient of L with respect to sites, densities and texels,
+ * given dL/dC per ray; accumulates into the outputs (the caller zeroes them).
+ *
+ * With g = dL/dC, S_k = sum_{m>k} w_m c_m + T_final bg:
+ *   dL/dtau_k   = g.(T_{k+1} c_k - S_k)              (tau_k = sigma delta_k)
+ *   dL/dsigma_k = dL/dtau_k * delta_k                 (matches Eq. 3)
+ *   dL/dc_k     = g * w_k  -> texels by bilinear weight
+ *   crossing b between walked cells k, k+1 at t_b, t_near' < t_b < t_far':
+ *     dL/dt_b = sigma_k dL/dtau_k - sigma_{k+1} dL/dtau_{k+1}
+ *     dt_b/ds_k     = (x_b - s_k) / (n.d)
+ *     dt_b/ds_{k+1} = (s_{k+1} - x_b) / (n.d),  n = s_{k+1} - s_k.
+ * When the walk stopped by transmittance inside (t_near', t_far'), the exit
+ * plane of the last cell still moves delta_K; its far side gets no dtau. */
+int vto_render_bwd(const vto_scene* sc, int64_t n_rays, const double* o, const double* d,
+                   const vto_params* p, const double* grad_rgb, double* g_sites, double* g_sigma,
+                   double* g_tex, int n_threads) {
+  if (n_threads < 1) n_threads = 1;
+  if (n_threads > 256) n_threads = 256;
+  if (n_rays < n_threads) n_threads = n_rays > 0 ? (int)n_rays : 1;
+  pthread_mutex_t mu;
+  pthread_mutex_init(&mu, NULL);
+  pthread_t th[256];
+  bwd_job jobs[256];
+  int64_t chunk = (n_rays + n_threads - 1) / n_threads;
+  for (int t = 0; t < n_threads; ++t) {
+    jobs[t].sc = sc;
+    jobs[t].p = p;
+    jobs[t].o = o;
+    jobs[t].d = d;
+    jobs[t].g = grad_rgb;
+    jobs[t].g_sites = g_sites;
+    jobs[t].g_sigma = g_sigma;
+    jobs[t].g_tex = g_tex;
+    jobs[t].mu = &mu;
+    jobs[t].lo = t * chunk;
+    jobs[t].hi = (t + 1) * chunk < n_rays ? (t + 1) * chunk : n_rays;
+    jobs[t].status = VTO_OK;
+    if (jobs[t].lo >= jobs[t].hi) continue;
+    if (n_threads == 1)
+      bwd_worker(&jobs[t]);
+    else
+      pthread_create(&th[t], NULL, bwd_worker, &jobs[t]);
+  }
+  int st = VTO_OK;
+  for (int t = 0; t < n_threads; ++t) {
+    if (jobs[t].lo >= jobs[t].hi) continue;
+    if (n_threads > 1) pthread_join(th[t], NULL);
+    if (jobs[t].status != VTO_OK) st = jobs[t].status;
+  }
+  pthread_mutex_destroy(&mu);
+  return st;
 }
 
 /* ------------------------------------------------------------------ */

@@ -1,0 +1,197 @@
+"""PyTorch-facing API over libvt.so.
+
+PyTorch supplies device memory and the current stream; every step of the
+rendering path runs in the library's CUDA kernels. ``VTRender`` is the
+``torch.autograd.Function``: its forward calls vt_render_fwd and saves only
+the output colours (no per-ray cell lists); its backward calls vt_render_bwd,
+which re-traverses each ray (recomputation in place of storing the walk).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _vt
+from ._vt import VT_BF16, VT_F16, VT_F32  # noqa: F401
+
+_DTYPES = {"f32": VT_F32, "fp32": VT_F32, "f16": VT_F16, "fp16": VT_F16, "bf16": VT_BF16}
+
+
+def _stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ptr(t):
+    return 0 if t is None else t.data_ptr()
+
+
+def _dev_f32(x, device):
+    return torch.as_tensor(x, dtype=torch.float32, device=device).contiguous()
+
+
+class Scene:
+    """A Voronoi scene resident on the GPU (library-owned, Morton-ordered)."""
+
+    def __init__(self, sites, sigma, tex, adj_offsets, adj_indices, tex_dtype="f32", device="cuda"):
+        device = torch.device(device)
+        self.device = device
+        sites = _dev_f32(sites, device)
+        sigma = _dev_f32(sigma, device)
+        tex = _dev_f32(tex, device)
+        off = torch.as_tensor(adj_offsets, dtype=torch.int64, device=device).contiguous()
+        idx = torch.as_tensor(adj_indices, dtype=torch.int32, device=device).contiguous()
+        n = sites.shape[0]
+        if sites.shape != (n, 3) or sigma.shape != (n,) or tex.dim() != 4 or tex.shape[0] != n \
+                or tex.shape[1] != tex.shape[2] or tex.shape[3] != 3 or off.shape != (n + 1,):
+            raise ValueError("bad scene shapes")
+        self.n, self.R = n, tex.shape[1]
+        self.tex_dtype = _DTYPES[tex_dtype] if isinstance(tex_dtype, str) else int(tex_dtype)
+        desc = _vt.vt_scene_desc(n, self.R, self.tex_dtype, sites.data_ptr(), sigma.data_ptr(), tex.data_ptr(),
+                                 off.data_ptr(), idx.data_ptr())
+        with torch.cuda.device(device):
+            self.handle = _vt.vt_scene_create(desc, _stream())
+        self.n_edges = _vt.vt_scene_info(self.handle)[3]
+
+    @classmethod
+    def from_workload(cls, sc, tex_dtype="f32", device="cuda"):
+        return cls(sc.sites, sc.sigma, sc.tex, sc.offsets, sc.indices, tex_dtype=tex_dtype, device=device)
+
+    def update(self, sites=None, sigma=None, tex=None):
+        keep = [None if x is None else _dev_f32(x, self.device) for x in (sites, sigma, tex)]
+        _vt.vt_scene_update(self.handle, *[_ptr(x) for x in keep], _stream())
+
+    def get_error(self):
+        """(status, fp64_rechecks) since the last call; synchronises the stream."""
+        return _vt.vt_scene_get_error(self.handle, _stream())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _vt.vt_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_params(t_near=0.0, t_far=20.0, use_clip_box=False, clip_lo=(0, 0, 0), clip_hi=(1, 1, 1), T_eps=1e-4,
+                skip_weight=0.0, bg=(1, 1, 1), img_w=0, img_h=0, n_images=0, max_steps=0):
+    p = _vt.vt_render_params()
+    p.t_near, p.t_far, p.use_clip_box = t_near, t_far, int(bool(use_clip_box))
+    p.clip_lo[:] = list(clip_lo)
+    p.clip_hi[:] = list(clip_hi)
+    p.T_eps, p.skip_weight = T_eps, skip_weight
+    p.bg[:] = list(bg)
+    p.img_w, p.img_h, p.n_images, p.max_steps = img_w, img_h, n_images, max_steps
+    return p
+
+
+def camera_struct(cam) -> _vt.vt_camera:
+    """vt_camera from a workloads.Camera-like object."""
+    c = _vt.vt_camera()
+    c.kind, c.w, c.h = cam.kind, cam.w, cam.h
+    c.eye[:] = list(cam.eye)
+    c.fwd[:] = list(cam.fwd)
+    c.up[:] = list(cam.up)
+    c.fov_y, c.fisheye_fov = cam.fov_y, cam.fisheye_fov
+    c.rs_velocity[:] = list(cam.rs_velocity)
+    c.lens_radius, c.focus_dist, c.lens_samples, c.seed = cam.lens_radius, cam.focus_dist, cam.lens_samples, cam.seed
+    return c
+
+
+def generate_rays(cameras, device="cuda", out=None):
+    """Rays of all cameras, in order [camera][row][col][lens sample]."""
+    cs = [camera_struct(c) for c in cameras]
+    n = sum(_vt.vt_camera_n_rays(c) for c in cs)
+    if out is None:
+        o = torch.empty(n, 3, device=device)
+        d = torch.empty(n, 3, device=device)
+        t = torch.empty(n, device=device)
+    else:
+        o, d, t = out
+    _vt.vt_generate_rays(cs, o.data_ptr(), d.data_ptr(), t.data_ptr(), _stream())
+    return o, d, t
+
+
+def render_fwd(scene: Scene, o, d, params, time=None, out=None, want_steps=True):
+    n = o.shape[0]
+    if out is None:
+        rgb = torch.empty(n, 3, device=o.device)
+        T = torch.empty(n, device=o.device)
+        steps = torch.empty(n, dtype=torch.int32, device=o.device) if want_steps else None
+    else:
+        rgb, T, steps = out
+    _vt.vt_render_fwd(scene.handle, n, o.data_ptr(), d.data_ptr(), _ptr(time), params, rgb.data_ptr(), _ptr(T),
+                      _ptr(steps), _stream())
+    return rgb, T, steps
+
+
+def render_bwd(scene: Scene, o, d, params, rgb, grad_rgb, time=None, out=None, need=(True, True, True)):
+    dev = o.device
+    if out is None:
+        gs = torch.empty(scene.n, 3, device=dev) if need[0] else None
+        gsig = torch.empty(scene.n, device=dev) if need[1] else None
+        gt = torch.empty(scene.n, scene.R, scene.R, 3, device=dev) if need[2] else None
+    else:
+        gs, gsig, gt = out
+    _vt.vt_render_bwd(scene.handle, o.shape[0], o.data_ptr(), d.data_ptr(), _ptr(time), params, rgb.data_ptr(),
+                      grad_rgb.contiguous().data_ptr(), _ptr(gs), _ptr(gsig), _ptr(gt), _stream())
+    return gs, gsig, gt
+
+
+def trace_cells(scene: Scene, o, d, params, max_cells=512):
+    n = o.shape[0]
+    cells = torch.full((n, max_cells), -1, dtype=torch.int32, device=o.device)
+    t_exit = torch.full((n, max_cells), float("nan"), device=o.device)
+    n_cells = torch.empty(n, dtype=torch.int32, device=o.device)
+    _vt.vt_trace_cells(scene.handle, n, o.data_ptr(), d.data_ptr(), params, max_cells, cells.data_ptr(),
+                       t_exit.data_ptr(), n_cells.data_ptr(), _stream())
+    return cells, t_exit, n_cells
+
+
+def l2_loss(rgb, target):
+    n = rgb.shape[0]
+    grad = torch.empty_like(rgb)
+    loss = torch.empty(1, device=rgb.device)
+    _vt.vt_l2_loss(n, rgb.data_ptr(), target.contiguous().data_ptr(), grad.data_ptr(), loss.data_ptr(), _stream())
+    return loss, grad
+
+
+def average_samples(rgb_rays, spp):
+    n_px = rgb_rays.shape[0] // spp
+    out = torch.empty(n_px, 3, device=rgb_rays.device)
+    _vt.vt_average_samples(n_px, spp, rgb_rays.data_ptr(), out.data_ptr(), _stream())
+    return out
+
+
+def average_samples_bwd(grad_px, spp):
+    out = torch.empty(grad_px.shape[0] * spp, 3, device=grad_px.device)
+    _vt.vt_average_samples_bwd(grad_px.shape[0], spp, grad_px.contiguous().data_ptr(), out.data_ptr(), _stream())
+    return out
+
+
+class VTRender(torch.autograd.Function):
+    """Differentiable render of rays (o, d) through a Scene.
+
+    The scene's sites / sigma / tex tensors are passed so that autograd knows
+    which leaves receive gradients; the Scene must hold their current values
+    (call scene.update after changing them)."""
+
+    @staticmethod
+    def forward(ctx, sites, sigma, tex, o, d, scene, params):
+        rgb, _, _ = render_fwd(scene, o, d, params, want_steps=False)
+        ctx.scene, ctx.params = scene, params
+        ctx.save_for_backward(o, d, rgb)
+        return rgb
+
+    @staticmethod
+    def backward(ctx, grad_rgb):
+        o, d, rgb = ctx.saved_tensors
+        need = ctx.needs_input_grad[:3]
+        gs, gsig, gt = render_bwd(ctx.scene, o, d, ctx.params, rgb, grad_rgb, need=need)
+        return gs, gsig, gt, None, None, None, None
+
+
+def render(sites, sigma, tex, o, d, scene: Scene, params):
+    return VTRender.apply(sites, sigma, tex, o, d, scene, params)

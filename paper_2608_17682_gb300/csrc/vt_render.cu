@@ -1,0 +1,635 @@
+// vt_render.cu -- start-cell search, Voronoi walk, compositing, adjoint.
+//
+// One thread per ray; a warp covers a 4 x 8 tile of an image (Sec. 5.6
+// "warp-coherent tiling") so neighbouring threads walk similar cells and
+// share cache lines. Forward, backward and trace are one templated kernel
+// whose walk is the same inline code, so their decisions are identical.
+//
+// Exit test (Sec. 3.1): from cell i, entered at ray parameter t, the exit is
+// the nearest forward crossing over the Delaunay neighbours j of
+//   dt_j = n.(r + n/2) / (n.d),   n = s_j - s_i,  r = s_i - (o + t d),
+// which is t_j - t for t_j = n.((s_i+s_j)/2 - o)/(n.d). r is formed with
+// compensated (float-float) arithmetic, so the comparison error scales with
+// the cell size instead of the distance from the origin. Candidates are
+// compared by cross-multiplication (no division in the loop). A plane with
+// |n.d| <= 1e-6 |n||d| (grazing; FP32 cannot fix the sign of n.d) is
+// re-evaluated in FP64 from the FP32 inputs.
+//
+// Compositing (Sec. 3.2): alpha = 1 - exp(-sigma delta), w = T alpha,
+// C += w c, T *= (1 - alpha); stop once T < T_eps after compositing a cell.
+// Colour (Sec. 5.1): bilinear fetch of the cell's octahedral texture at the
+// ray direction; the four taps are fixed per ray.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "vt_internal.cuh"
+
+namespace {
+
+enum Mode { FWD = 0, BWD = 1, TRACE = 2 };
+
+struct Scene {
+  const float4* __restrict__ site;
+  const int4* __restrict__ meta;
+  const float4* __restrict__ nbr;
+  const void* __restrict__ tex;
+  int64_t n;
+  int32_t R, RR;
+  unsigned long long* err;
+};
+
+struct RP {  // render parameters, device copy
+  float t_near, t_far;
+  int clip;
+  float3 lo, hi;
+  float T_eps, skip;
+  float3 bg;
+  int img_w, img_h, n_images, tiles_x, tiles_per_img;
+  int max_steps;
+  int64_t n_rays;
+  int64_t anchor_stride;
+};
+
+struct Grad {
+  float4* g_cell;
+  float4* g_tex;
+  const float* rgb;
+  const float* grad;
+};
+
+struct Trace {
+  int32_t* cells;
+  float* t_exit;
+  int32_t* n_cells;
+  int max_cells;
+};
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ float dist2(float3 q, float x, float y, float z) {
+  float dx = __fsub_rn(q.x, x), dy = __fsub_rn(q.y, y), dz = __fsub_rn(q.z, z);
+  return __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// s - (o + (th + tl) d), compensated per component
+__device__ __forceinline__ float rel1(float s, float o, float d, float th, float tl) {
+  float ah, al;
+  two_sum(s, -o, ah, al);
+  float ph = __fmul_rn(th, d);
+  float pl = __fmaf_rn(th, d, -ph);
+  pl = __fmaf_rn(tl, d, pl);
+  return __fadd_rn(__fsub_rn(ah, ph), __fsub_rn(al, pl));
+}
+__device__ __forceinline__ float3 rel_pos(float3 s, float3 o, float3 d, float th, float tl) {
+  return make_float3(rel1(s.x, o.x, d.x, th, tl), rel1(s.y, o.y, d.y, th, tl), rel1(s.z, o.z, d.z, th, tl));
+}
+
+// (th, tl) + x  -> renormalised float-float
+__device__ __forceinline__ void ff_add(float& th, float& tl, float x) {
+  float s, e;
+  two_sum(th, x, s, e);
+  e = __fadd_rn(e, tl);
+  th = __fadd_rn(s, e);
+  tl = __fsub_rn(e, __fsub_rn(th, s));
+}
+// float-float strictly greater / greater-or-equal than a float
+__device__ __forceinline__ bool ff_gt(float th, float tl, float x) { return th > x || (th == x && tl > 0.f); }
+__device__ __forceinline__ bool ff_ge(float th, float tl, float x) { return th > x || (th == x && tl >= 0.f); }
+
+__device__ __forceinline__ float4 load_texel(const void* tex, int64_t e, int DT) {
+  if (DT == VT_F32) return __ldg(reinterpret_cast<const float4*>(tex) + e);
+  uint2 u = __ldg(reinterpret_cast<const uint2*>(tex) + e);
+  if (DT == VT_F16) {
+    __half2 a = *reinterpret_cast<__half2*>(&u.x), b = *reinterpret_cast<__half2*>(&u.y);
+    float2 fa = __half22float2(a), fb = __half22float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+  }
+  return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u), __uint_as_float(u.y << 16),
+                     __uint_as_float(u.y & 0xffff0000u));
+}
+
+// Octahedral map (Sec. 5.1) + bilinear taps, texel index y*R + x, clamp to edge.
+__device__ __forceinline__ void taps_for(float3 d, int R, int tap[4], float tw[4]) {
+  float l1 = __fadd_rn(__fadd_rn(fabsf(d.x), fabsf(d.y)), fabsf(d.z));
+  float qx = __fdiv_rn(d.x, l1), qy = __fdiv_rn(d.y, l1);
+  float u, v;
+  if (d.z >= 0.f) {
+    u = qx;
+    v = qy;
+  } else {
+    u = copysignf(__fsub_rn(1.f, fabsf(qy)), qx >= 0.f ? 1.f : -1.f);
+    v = copysignf(__fsub_rn(1.f, fabsf(qx)), qy >= 0.f ? 1.f : -1.f);
+  }
+  float x = __fsub_rn(__fmul_rn(__fmul_rn(__fadd_rn(u, 1.f), 0.5f), (float)R), 0.5f);
+  float y = __fsub_rn(__fmul_rn(__fmul_rn(__fadd_rn(v, 1.f), 0.5f), (float)R), 0.5f);
+  x = fminf(fmaxf(x, 0.f), (float)(R - 1));
+  y = fminf(fmaxf(y, 0.f), (float)(R - 1));
+  int x0 = min((int)floorf(x), R - 1), y0 = min((int)floorf(y), R - 1);
+  int x1 = min(x0 + 1, R - 1), y1 = min(y0 + 1, R - 1);
+  float fx = __fsub_rn(x, (float)x0), fy = __fsub_rn(y, (float)y0);
+  tap[0] = y0 * R + x0;
+  tap[1] = y0 * R + x1;
+  tap[2] = y1 * R + x0;
+  tap[3] = y1 * R + x1;
+  tw[0] = __fmul_rn(__fsub_rn(1.f, fx), __fsub_rn(1.f, fy));
+  tw[1] = __fmul_rn(fx, __fsub_rn(1.f, fy));
+  tw[2] = __fmul_rn(__fsub_rn(1.f, fx), fy);
+  tw[3] = __fmul_rn(fx, fy);
+}
+
+// Greedy descent on the Delaunay graph to the site nearest q, ordering sites
+// by (FP32 squared distance, user id). Each move strictly decreases that key,
+// so it ends; a local minimum over the Delaunay neighbours is the nearest
+// site (Delaunay property).
+__device__ int greedy_nearest(const Scene& S, int cell, float3 q, int max_steps, bool& ok) {
+  float4 s0 = __ldg(S.site + cell);
+  float best = dist2(q, s0.x, s0.y, s0.z);
+  int best_uid = __ldg(&S.meta[cell].w);
+  for (int it = 0; it < max_steps; ++it) {
+    int4 m = __ldg(S.meta + cell);
+    int bc = cell;
+    for (int p = m.x; p < m.y; ++p) {
+      float4 r = __ldg(S.nbr + p);
+      float dd = dist2(q, r.x, r.y, r.z);
+      if (dd <= best) {
+        int j = __float_as_int(r.w);
+        int uid = __ldg(&S.meta[j].w);
+        if (dd < best || uid < best_uid) {
+          best = dd;
+          best_uid = uid;
+          bc = j;
+        }
+      }
+    }
+    if (bc == cell) return cell;
+    cell = bc;
+  }
+  ok = false;
+  return cell;
+}
+
+// ---------------------------------------------------------------- anchors
+// Exact nearest site of each anchor point: packed (distance bits, user id)
+// atomicMin over all sites; blockIdx.y selects the anchor.
+__global__ void k_anchor_nn(Scene S, const float* __restrict__ o, int64_t stride, unsigned long long* key) {
+  int a = blockIdx.y;
+  float3 q = make_float3(o[3 * a * stride], o[3 * a * stride + 1], o[3 * a * stride + 2]);
+  unsigned long long best = ~0ull;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.n; i += (int64_t)gridDim.x * blockDim.x) {
+    float4 s = __ldg(S.site + i);
+    float dd = dist2(q, s.x, s.y, s.z);
+    unsigned long long k = ((unsigned long long)__float_as_uint(dd) << 32) | (unsigned)__ldg(&S.meta[i].w);
+    best = k < best ? k : best;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    unsigned long long v = __shfl_xor_sync(0xffffffffu, best, off);
+    best = v < best ? v : best;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMin(key + a, best);
+}
+
+__global__ void k_anchor_refine(Scene S, const float* __restrict__ o, int64_t stride, int n_anchors,
+                                const int32_t* __restrict__ inv, const unsigned long long* key, int32_t* cell,
+                                int max_steps) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n_anchors) return;
+  float3 q = make_float3(o[3 * a * stride], o[3 * a * stride + 1], o[3 * a * stride + 2]);
+  int c = inv[(int)(key[a] & 0xffffffffu)];
+  bool ok = true;
+  c = greedy_nearest(S, c, q, max_steps, ok);
+  if (!ok) atomicOr(S.err, (unsigned long long)VT_EBIT_MAX_STEPS);
+  cell[a] = c;
+}
+
+// ---------------------------------------------------------------- ray mapping
+__device__ __forceinline__ int64_t ray_of_thread(const RP& P, int64_t tid) {
+  if (P.img_w <= 0) return tid < P.n_rays ? tid : -1;
+  int64_t warp = tid >> 5;
+  int lane = (int)(tid & 31);
+  int64_t img = warp / P.tiles_per_img;
+  if (img >= P.n_images) return -1;
+  int t = (int)(warp - img * P.tiles_per_img);
+  int ty = t / P.tiles_x, tx = t - ty * P.tiles_x;
+  int x = tx * 8 + (lane & 7), y = ty * 4 + (lane >> 3);
+  if (x >= P.img_w || y >= P.img_h) return -1;
+  return (img * P.img_h + y) * (int64_t)P.img_w + x;
+}
+
+// ---------------------------------------------------------------- the walk
+template <int MODE, int DT>
+__global__ void __launch_bounds__(256) k_walk(Scene S, RP P, const float* __restrict__ O, const float* __restrict__ D,
+                                              const int32_t* __restrict__ anchor_cell, float* __restrict__ rgb_out,
+                                              float* __restrict__ T_out, int32_t* __restrict__ steps_out, Grad G,
+                                              Trace TR) {
+  const int64_t ray = ray_of_thread(P, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+  if (ray < 0) return;
+  const float3 o = make_float3(O[3 * ray], O[3 * ray + 1], O[3 * ray + 2]);
+  const float3 d = make_float3(D[3 * ray], D[3 * ray + 1], D[3 * ray + 2]);
+  const float dd = __fmaf_rn(d.x, d.x, __fmaf_rn(d.y, d.y, __fmul_rn(d.z, d.z)));
+  float C0 = 0.f, C1 = 0.f, C2 = 0.f;
+  float T = 1.f;
+  int k = 0;
+  bool bad = !(dd > 0.f) || !isfinite(dd) || !isfinite(o.x) || !isfinite(o.y) || !isfinite(o.z);
+  // clip [t_near, t_far] to the optional box (slab test)
+  float t0 = P.t_near, t1 = P.t_far;
+  if (P.clip && !bad) {
+    const float ov[3] = {o.x, o.y, o.z}, dv[3] = {d.x, d.y, d.z};
+    const float lv[3] = {P.lo.x, P.lo.y, P.lo.z}, hv[3] = {P.hi.x, P.hi.y, P.hi.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (dv[a] != 0.f) {
+        float ta = __fdiv_rn(__fsub_rn(lv[a], ov[a]), dv[a]), tb = __fdiv_rn(__fsub_rn(hv[a], ov[a]), dv[a]);
+        t0 = fmaxf(t0, fminf(ta, tb));
+        t1 = fminf(t1, fmaxf(ta, tb));
+      } else if (ov[a] < lv[a] || ov[a] > hv[a]) {
+        t1 = t0;
+      }
+    }
+  }
+  // BWD inputs
+  float g0 = 0.f, g1 = 0.f, g2 = 0.f, Co0 = 0.f, Co1 = 0.f, Co2 = 0.f;
+  if (MODE == BWD) {
+    g0 = G.grad[3 * ray];
+    g1 = G.grad[3 * ray + 1];
+    g2 = G.grad[3 * ray + 2];
+    Co0 = G.rgb[3 * ray];
+    Co1 = G.rgb[3 * ray + 1];
+    Co2 = G.rgb[3 * ray + 2];
+  }
+  if (bad) {
+    atomicOr(S.err, (unsigned long long)VT_EBIT_BAD_RAY);
+  } else if (t1 > t0) {
+    int tap[4];
+    float tw[4];
+    taps_for(d, S.R, tap, tw);
+    const float G2dd = __fmul_rn(1e-12f, dd);  // grazing: (n.d)^2 <= 1e-12 |n|^2 |d|^2
+    const double3 o64 = make_double3(o.x, o.y, o.z), d64 = make_double3(d.x, d.y, d.z);
+    // start cell: greedy walk from this ray's anchor cell to the origin
+    bool ok = true;
+    int cell = greedy_nearest(S, anchor_cell[ray / P.anchor_stride], o, P.max_steps, ok);
+    if (!ok) atomicOr(S.err, (unsigned long long)VT_EBIT_MAX_STEPS);
+    float4 s4 = __ldg(S.site + cell);
+    float3 si = make_float3(s4.x, s4.y, s4.z);
+    float th = 0.f, tl = 0.f;  // entry parameter of the current cell (float-float)
+    float A0 = 0.f, A1 = 0.f, A2 = 0.f;  // BWD: prefix of w c (inclusive)
+    // BWD carry: previous cell
+    int pc = -1;
+    float p_sig = 0.f, p_dtau = 0.f, p_gsig = 0.f;
+    float3 p_gs = make_float3(0.f, 0.f, 0.f), p_s = si;
+    bool cross_valid = false;
+    float3 cross_n = make_float3(0.f, 0.f, 0.f);
+    for (;;) {
+      if (k >= P.max_steps) {
+        atomicOr(S.err, (unsigned long long)VT_EBIT_MAX_STEPS);
+        break;
+      }
+      const int4 m = __ldg(S.meta + cell);
+      const float sig = __int_as_float(m.z);
+      // texels of this cell (independent of the exit search)
+      float4 tx[4];
+      if (MODE != TRACE) {
+        const int64_t base = (int64_t)cell * S.RR;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tx[q] = load_texel(S.tex, base + tap[q], DT);
+      }
+      const float3 r = rel_pos(si, o, d, th, tl);
+      // ---- exit search over the Delaunay neighbours
+      float bn = 1.f, bd = 0.f;  // best dt = bn / bd (bd == 0: none yet)
+      int bj = -1;
+      float3 bq = si;
+      for (int p = m.x; p < m.y; ++p) {
+        const float4 q = __ldg(S.nbr + p);
+        const float nx = __fsub_rn(q.x, si.x), ny = __fsub_rn(q.y, si.y), nz = __fsub_rn(q.z, si.z);
+        float den = __fmaf_rn(nx, d.x, __fmaf_rn(ny, d.y, __fmul_rn(nz, d.z)));
+        const float nn = __fmaf_rn(nx, nx, __fmaf_rn(ny, ny, __fmul_rn(nz, nz)));
+        float num = __fmaf_rn(nx, r.x, __fmaf_rn(ny, r.y, __fmaf_rn(nz, r.z, __fmul_rn(0.5f, nn))));
+        if (__fmul_rn(den, den) <= __fmul_rn(G2dd, nn)) {
+          // grazing plane: FP64 recheck from the FP32 inputs
+          atomicAdd(S.err + 1, 1ull);
+          const double t64 = (double)th + (double)tl;
+          const double n0 = (double)q.x - (double)si.x, n1 = (double)q.y - (double)si.y,
+                       n2 = (double)q.z - (double)si.z;
+          const double den64 = n0 * d64.x + n1 * d64.y + n2 * d64.z;
+          if (!(den64 > 0.0)) continue;
+          const double r0 = (double)si.x - (o64.x + t64 * d64.x), r1 = (double)si.y - (o64.y + t64 * d64.y),
+                       r2 = (double)si.z - (o64.z + t64 * d64.z);
+          const double num64 = n0 * r0 + n1 * r1 + n2 * r2 + 0.5 * (n0 * n0 + n1 * n1 + n2 * n2);
+          num = (float)(num64 / den64);
+          den = 1.f;
+        } else if (!(den > 0.f)) {
+          continue;
+        }
+        if (__fmul_rn(num, bd) < __fmul_rn(bn, den)) {
+          bn = num;
+          bd = den;
+          bj = __float_as_int(q.w);
+          bq = make_float3(q.x, q.y, q.z);
+        }
+      }
+      ++k;
+      const float dt = bj >= 0 ? __fdiv_rn(bn, bd) : INFINITY;
+      float eh = th, el = tl;  // exit parameter
+      if (bj >= 0)
+        ff_add(eh, el, dt);
+      else
+        eh = INFINITY, el = 0.f;
+      const bool exit_beyond = bj < 0 || ff_ge(eh, el, t1);
+      if (MODE == TRACE) {
+        const int64_t slot = ray * (int64_t)TR.max_cells + (k - 1);
+        if (k <= TR.max_cells) {
+          TR.cells[slot] = m.w;
+          if (TR.t_exit) TR.t_exit[slot] = bj >= 0 ? __fadd_rn(eh, el) : INFINITY;
+        }
+      }
+      // ---- segment [max(t_in, t0), min(t_exit, t1)]
+      const bool start_clip = !ff_ge(th, tl, t0);
+      float delta;
+      if (!start_clip && !exit_beyond) {
+        delta = dt;
+      } else {
+        float ah = th, al = tl, bh = eh, bl = el;
+        if (start_clip) ah = t0, al = 0.f;
+        if (exit_beyond) bh = t1, bl = 0.f;
+        delta = __fadd_rn(__fsub_rn(bh, ah), __fsub_rn(bl, al));
+      }
+      bool stop = false;
+      float dtau = 0.f, w = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+      bool coloured = false;
+      if (delta > 0.f) {
+        const float e = expf(-__fmul_rn(sig, delta));
+        const float alpha = __fsub_rn(1.f, e);
+        w = __fmul_rn(T, alpha);
+        const float Tn = __fmul_rn(T, e);
+        if (MODE != TRACE && (!(P.skip > 0.f) || w >= P.skip)) {
+          coloured = true;
+          c0 = __fmaf_rn(tw[3], tx[3].x, __fmaf_rn(tw[2], tx[2].x, __fmaf_rn(tw[1], tx[1].x, __fmul_rn(tw[0], tx[0].x))));
+          c1 = __fmaf_rn(tw[3], tx[3].y, __fmaf_rn(tw[2], tx[2].y, __fmaf_rn(tw[1], tx[1].y, __fmul_rn(tw[0], tx[0].y))));
+          c2 = __fmaf_rn(tw[3], tx[3].z, __fmaf_rn(tw[2], tx[2].z, __fmaf_rn(tw[1], tx[1].z, __fmul_rn(tw[0], tx[0].z))));
+          if (MODE == FWD) {
+            C0 = __fmaf_rn(w, c0, C0);
+            C1 = __fmaf_rn(w, c1, C1);
+            C2 = __fmaf_rn(w, c2, C2);
+          } else {
+            A0 = __fmaf_rn(w, c0, A0);
+            A1 = __fmaf_rn(w, c1, A1);
+            A2 = __fmaf_rn(w, c2, A2);
+          }
+        }
+        if (MODE == BWD) {
+          // dL/dtau_k = g . (T_{k+1} c_k - S_k),  S_k = C_out - A_k
+          dtau = g0 * (Tn * c0 - (Co0 - A0)) + g1 * (Tn * c1 - (Co1 - A1)) + g2 * (Tn * c2 - (Co2 - A2));
+        }
+        T = Tn;
+        if (T < P.T_eps) stop = true;
+      }
+      if (MODE == BWD) {
+        // crossing between the previous cell and this one (entry face)
+        float3 gs = make_float3(0.f, 0.f, 0.f);
+        if (pc >= 0 && cross_valid) {
+          const float nd = __fmaf_rn(cross_n.x, d.x, __fmaf_rn(cross_n.y, d.y, cross_n.z * d.z));
+          const float dtb = (p_sig * p_dtau - sig * dtau) / nd;
+          // x_b - s_prev = n - r ; s_cur - x_b = r
+          p_gs.x += dtb * (cross_n.x - r.x);
+          p_gs.y += dtb * (cross_n.y - r.y);
+          p_gs.z += dtb * (cross_n.z - r.z);
+          gs = make_float3(dtb * r.x, dtb * r.y, dtb * r.z);
+        }
+        if (pc >= 0 && (p_gs.x != 0.f || p_gs.y != 0.f || p_gs.z != 0.f || p_gsig != 0.f))
+          atomicAdd(G.g_cell + pc, make_float4(p_gs.x, p_gs.y, p_gs.z, p_gsig));
+        if (coloured && w > 0.f) {
+          const int64_t base = (int64_t)cell * S.RR;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float ww = w * tw[q];
+            if (ww != 0.f) atomicAdd(G.g_tex + base + tap[q], make_float4(g0 * ww, g1 * ww, g2 * ww, 0.f));
+          }
+        }
+        pc = cell;
+        p_sig = sig;
+        p_dtau = dtau;
+        p_gsig = dtau * delta;
+        p_gs = gs;
+        p_s = si;
+        // will the crossing at this cell's exit be differentiable?
+        cross_valid = (bj >= 0) && !exit_beyond && ff_gt(eh, el, t0);
+        if (bj >= 0) cross_n = make_float3(__fsub_rn(bq.x, si.x), __fsub_rn(bq.y, si.y), __fsub_rn(bq.z, si.z));
+        if (stop && cross_valid) {
+          // terminated inside the extent: the exit plane still moves delta_K
+          const float3 re = rel_pos(si, o, d, eh, el);  // s_K - x_out
+          const float nd = __fmaf_rn(cross_n.x, d.x, __fmaf_rn(cross_n.y, d.y, cross_n.z * d.z));
+          const float dtb = (p_sig * p_dtau) / nd;
+          p_gs.x -= dtb * re.x;
+          p_gs.y -= dtb * re.y;
+          p_gs.z -= dtb * re.z;
+          atomicAdd(G.g_cell + bj,
+                    make_float4(dtb * (re.x + cross_n.x), dtb * (re.y + cross_n.y), dtb * (re.z + cross_n.z), 0.f));
+        }
+      }
+      if (stop || exit_beyond) break;
+      cell = bj;
+      si = bq;
+      th = eh;
+      tl = el;
+    }
+    if (MODE == BWD && pc >= 0 && (p_gs.x != 0.f || p_gs.y != 0.f || p_gs.z != 0.f || p_gsig != 0.f))
+      atomicAdd(G.g_cell + pc, make_float4(p_gs.x, p_gs.y, p_gs.z, p_gsig));
+    (void)p_s;
+    C0 = __fmaf_rn(T, P.bg.x, C0);
+    C1 = __fmaf_rn(T, P.bg.y, C1);
+    C2 = __fmaf_rn(T, P.bg.z, C2);
+  } else {
+    C0 = P.bg.x;
+    C1 = P.bg.y;
+    C2 = P.bg.z;
+  }
+  if (MODE == FWD) {
+    rgb_out[3 * ray] = C0;
+    rgb_out[3 * ray + 1] = C1;
+    rgb_out[3 * ray + 2] = C2;
+    if (T_out) T_out[ray] = T;
+    if (steps_out) steps_out[ray] = k;
+  } else if (MODE == TRACE) {
+    TR.n_cells[ray] = k;
+    if (k > TR.max_cells) atomicOr(S.err, (unsigned long long)VT_EBIT_CAPACITY);
+  }
+}
+
+// user-order gradients from the Morton-ordered scratch (overwrites outputs)
+__global__ void k_grad_out(int64_t n, int RR, const int4* __restrict__ meta, const float4* __restrict__ g_cell,
+                           const float4* __restrict__ g_tex, float* gs, float* gsig, float* gtex) {
+  int64_t total = n * RR;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / RR, t = e - i * RR;
+    int64_t u = __ldg(&meta[i].w);
+    if (gtex) {
+      float4 g = g_tex[e];
+      float* dst = gtex + (u * RR + t) * 3;
+      dst[0] = g.x;
+      dst[1] = g.y;
+      dst[2] = g.z;
+    }
+    if (t == 0) {
+      float4 c = g_cell[i];
+      if (gs) {
+        gs[3 * u] = c.x;
+        gs[3 * u + 1] = c.y;
+        gs[3 * u + 2] = c.z;
+      }
+      if (gsig) gsig[u] = c.w;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- host side
+vt_status make_rp(const vt_scene* s, int64_t n_rays, const vt_render_params* p, RP& P) {
+  if (!p) return VT_ERR_INVALID_ARG;
+  P.t_near = p->t_near;
+  P.t_far = p->t_far;
+  P.clip = p->use_clip_box != 0;
+  P.lo = make_float3(p->clip_lo[0], p->clip_lo[1], p->clip_lo[2]);
+  P.hi = make_float3(p->clip_hi[0], p->clip_hi[1], p->clip_hi[2]);
+  P.T_eps = p->T_eps;
+  P.skip = p->skip_weight;
+  P.bg = make_float3(p->bg[0], p->bg[1], p->bg[2]);
+  P.img_w = p->img_w;
+  P.img_h = p->img_h;
+  P.n_images = p->n_images;
+  P.n_rays = n_rays;
+  int64_t ms = p->max_steps > 0 ? p->max_steps : (s->n * 4 < (1 << 20) ? s->n * 4 : (1 << 20));
+  if (ms < 4) ms = 4;
+  P.max_steps = (int)ms;
+  if (!(p->t_far >= p->t_near) || !isfinite(p->t_near) || !(p->T_eps >= 0.f)) return VT_ERR_INVALID_ARG;
+  int64_t per_image;
+  if (p->img_w > 0) {
+    if (p->img_h <= 0 || p->n_images <= 0) return VT_ERR_INVALID_ARG;
+    per_image = (int64_t)p->img_w * p->img_h;
+    if (per_image * p->n_images != n_rays) return VT_ERR_INVALID_ARG;
+    P.tiles_x = (p->img_w + 7) / 8;
+    P.tiles_per_img = P.tiles_x * ((p->img_h + 3) / 4);
+    int64_t groups = (p->n_images + VT_MAX_ANCHORS - 1) / VT_MAX_ANCHORS;
+    P.anchor_stride = per_image * groups;
+  } else {
+    P.tiles_x = P.tiles_per_img = 0;
+    int64_t st = (n_rays + VT_MAX_ANCHORS - 1) / VT_MAX_ANCHORS;
+    P.anchor_stride = st < 4096 ? 4096 : st;
+  }
+  return VT_OK;
+}
+
+int64_t walk_threads(const RP& P) {
+  if (P.img_w <= 0) return P.n_rays;
+  return (int64_t)P.n_images * P.tiles_per_img * 32;
+}
+
+Scene scene_view(vt_scene* s) {
+  Scene S;
+  S.site = s->site;
+  S.meta = s->meta;
+  S.nbr = s->nbr;
+  S.tex = s->tex;
+  S.n = s->n;
+  S.R = s->R;
+  S.RR = s->R * s->R;
+  S.err = s->d_err;
+  return S;
+}
+
+vt_status anchors(vt_scene* s, const Scene& S, const RP& P, const float* o, cudaStream_t st) {
+  int na = (int)((P.n_rays + P.anchor_stride - 1) / P.anchor_stride);
+  if (na < 1 || na > VT_MAX_ANCHORS) return VT_ERR_INVALID_ARG;
+  VT_CUDA_TRY(cudaMemsetAsync(s->anchor_key, 0xff, na * sizeof(unsigned long long), st));
+  dim3 g(vt_grid(s->n, 256, 152 * 2), na);
+  k_anchor_nn<<<g, 256, 0, st>>>(S, o, P.anchor_stride, s->anchor_key);
+  k_anchor_refine<<<1, 64, 0, st>>>(S, o, P.anchor_stride, na, s->inv, s->anchor_key, s->anchor_cell, P.max_steps);
+  VT_CUDA_TRY(cudaGetLastError());
+  return VT_OK;
+}
+
+template <int MODE>
+vt_status launch_walk(vt_scene* s, const Scene& S, const RP& P, const float* o, const float* d, float* rgb,
+                      float* T, int32_t* steps, Grad G, Trace TR, cudaStream_t st) {
+  int64_t nt = walk_threads(P);
+  if (nt == 0) return VT_OK;
+  int g = vt_grid(nt, 256, ((int64_t)1 << 31) - 1);
+  if (s->dtype == VT_F32)
+    k_walk<MODE, VT_F32><<<g, 256, 0, st>>>(S, P, o, d, s->anchor_cell, rgb, T, steps, G, TR);
+  else if (s->dtype == VT_F16)
+    k_walk<MODE, VT_F16><<<g, 256, 0, st>>>(S, P, o, d, s->anchor_cell, rgb, T, steps, G, TR);
+  else
+    k_walk<MODE, VT_BF16><<<g, 256, 0, st>>>(S, P, o, d, s->anchor_cell, rgb, T, steps, G, TR);
+  VT_CUDA_TRY(cudaGetLastError());
+  return VT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vt_status vt_render_fwd(vt_scene* s, int64_t n_rays, const float* o, const float* d, const float* time,
+                        const vt_render_params* p, float* rgb_out, float* T_out, int32_t* steps_out,
+                        void* stream) {
+  (void)time;
+  if (!s || n_rays < 0 || (n_rays > 0 && (!o || !d || !rgb_out))) return VT_ERR_INVALID_ARG;
+  if (n_rays == 0) return VT_OK;
+  RP P;
+  vt_status r = make_rp(s, n_rays, p, P);
+  if (r != VT_OK) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  Scene S = scene_view(s);
+  r = anchors(s, S, P, o, st);
+  if (r != VT_OK) return r;
+  return launch_walk<FWD>(s, S, P, o, d, rgb_out, T_out, steps_out, Grad{}, Trace{}, st);
+}
+
+vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float* d, const float* time,
+                        const vt_render_params* p, const float* rgb_out, const float* grad_rgb, float* grad_sites,
+                        float* grad_sigma, float* grad_tex, void* stream) {
+  (void)time;
+  if (!s || n_rays < 0 || (n_rays > 0 && (!o || !d || !rgb_out || !grad_rgb))) return VT_ERR_INVALID_ARG;
+  RP P;
+  vt_status r = make_rp(s, n_rays > 0 ? n_rays : 0, p, P);
+  if (r != VT_OK && n_rays > 0) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t RR = (int64_t)s->R * s->R;
+  if (!s->g_cell) VT_CUDA_TRY(cudaMalloc(&s->g_cell, s->n * sizeof(float4)));
+  if (!s->g_tex) VT_CUDA_TRY(cudaMalloc(&s->g_tex, s->n * RR * sizeof(float4)));
+  VT_CUDA_TRY(cudaMemsetAsync(s->g_cell, 0, s->n * sizeof(float4), st));
+  VT_CUDA_TRY(cudaMemsetAsync(s->g_tex, 0, s->n * RR * sizeof(float4), st));
+  Scene S = scene_view(s);
+  if (n_rays > 0) {
+    r = anchors(s, S, P, o, st);
+    if (r != VT_OK) return r;
+    Grad G{s->g_cell, s->g_tex, rgb_out, grad_rgb};
+    r = launch_walk<BWD>(s, S, P, o, d, nullptr, nullptr, nullptr, G, Trace{}, st);
+    if (r != VT_OK) return r;
+  }
+  if (grad_sites || grad_sigma || grad_tex) {
+    k_grad_out<<<vt_grid(s->n * RR, 256, 152 * 64), 256, 0, st>>>(s->n, (int)RR, s->meta, s->g_cell, s->g_tex,
+                                                                    grad_sites, grad_sigma, grad_tex);
+    VT_CUDA_TRY(cudaGetLastError());
+  }
+  return VT_OK;
+}
+
+vt_status vt_trace_cells(vt_scene* s, int64_t n_rays, const float* o, const float* d, const vt_render_params* p,
+                         int32_t max_cells, int32_t* cells, float* t_exit, int32_t* n_cells, void* stream) {
+  if (!s || n_rays < 0 || max_cells < 0 || (n_rays > 0 && (!o || !d || !n_cells || (max_cells > 0 && !cells))))
+    return VT_ERR_INVALID_ARG;
+  if (n_rays == 0) return VT_OK;
+  RP P;
+  vt_status r = make_rp(s, n_rays, p, P);
+  if (r != VT_OK) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  Scene S = scene_view(s);
+  r = anchors(s, S, P, o, st);
+  if (r != VT_OK) return r;
+  Trace TR{cells, t_exit, n_cells, max_cells};
+  return launch_walk<TRACE>(s, S, P, o, d, nullptr, nullptr, nullptr, Grad{}, TR, st);
+}
+
+}  // extern "C"

@@ -1,0 +1,388 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Bars: cell sequences bit-exact for rays outside the degenerate band (the
+oracle flags rays that pass within 1e-6 of another face, start within 1e-6
+of a face, cross near t_near'/t_far', or sit within 1e-4 relative of the
+T / skip thresholds); images within 1e-4 max abs per channel (FP32 textures);
+gradients within |g - g_ref| <= 1e-3 max(|g_ref|, 1e-3 max|g_ref|).
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import oracle as O  # noqa: E402
+from paper_2608_17682_gb300 import workloads as W  # noqa: E402
+from paper_2608_17682_gb300 import api  # noqa: E402
+
+DEV = "cuda"
+IMG_TOL = 1e-4
+GRAD_REL = 1e-3
+
+
+def gpu_params(p, **kw):
+    q = dict(p)
+    q.update(kw)
+    return api.make_params(**q)
+
+
+def oracle_params(p, **kw):
+    q = {k: v for k, v in p.items() if k not in ("img_w", "img_h", "n_images", "max_steps")}
+    q.update({k: v for k, v in kw.items() if k not in ("img_w", "img_h", "n_images")})
+    return O.make_params(**q)
+
+
+def to_dev(*a):
+    return [torch.as_tensor(x, device=DEV).contiguous() for x in a]
+
+
+def compare_sequences(gc, gn, oc, on, flags):
+    """Cell sequences equal for every unflagged ray; returns (#checked, #flagged-mismatch)."""
+    ok = (flags & O.BAND_FLAGS) == 0
+    same = (gn == on) & np.all(gc == oc, axis=1)
+    bad = ok & ~same
+    assert not bad.any(), f"{bad.sum()} unflagged rays differ, first {np.nonzero(bad)[0][:5]}"
+    return int(ok.sum()), int((~ok & ~same).sum())
+
+
+def grad_close(g, ref, name):
+    g = np.asarray(g, np.float64)
+    ref = np.asarray(ref, np.float64)
+    floor = 1e-3 * np.abs(ref).max()
+    tol = GRAD_REL * np.maximum(np.abs(ref), floor)
+    err = np.abs(g - ref)
+    bad = err > tol
+    assert not bad.any(), (f"{name}: {bad.sum()} / {bad.size} entries off; worst rel "
+                           f"{(err / np.maximum(np.abs(ref), floor)).max():.3g}")
+
+
+# ---------------------------------------------------------------- fixtures
+
+@pytest.fixture(scope="module")
+def tiny():
+    wl = W.make_workload("tiny")
+    o, d = W.workload_rays(wl)
+    return wl, O.OracleScene.from_workload_scene(wl.scene), o, d
+
+
+@pytest.fixture(scope="module")
+def medium():
+    """50k-site surface-concentrated scene (several hundred tiles, ragged image)."""
+    sc = W.make_scene("surface", 50_000, 8, 77)
+    cams = [W.look_at_camera(0, 203, 121, W.orbit_eye(np.zeros(3), 3.0, az, 20.0), np.zeros(3))
+            for az in (30.0, 210.0)]
+    rng = np.random.default_rng(78)
+    os_, ds = [], []
+    for c in cams:
+        o, d = W.frustum_rays(c.eye, np.zeros(3), c.w, c.h, rng)
+        os_.append(o)
+        ds.append(d)
+    return sc, O.OracleScene.from_workload_scene(sc), np.concatenate(os_), np.concatenate(ds), cams
+
+
+# ---------------------------------------------------------------- forward
+
+@pytest.mark.parametrize("layout", ["image", "1d"])
+def test_tiny_forward_parity(tiny, layout):
+    wl, osc, o, d = tiny
+    scene = api.Scene.from_workload(wl.scene)
+    img = dict(img_w=64, img_h=64, n_images=1) if layout == "image" else {}
+    P = gpu_params(wl.params, **img)
+    to, td = to_dev(o, d)
+    rgb, T, steps = api.render_fwd(scene, to, td, P)
+    cells, t_exit, n_cells = api.trace_cells(scene, to, td, P, max_cells=256)
+    assert scene.get_error()[0] == 0
+    orgb, oT, osteps, flags = O.render(osc, o, d, params=oracle_params(wl.params))
+    oc, ot, on, _ = O.trace(osc, o, d, max_cells=256, params=oracle_params(wl.params))
+    ok = (flags & O.BAND_FLAGS) == 0
+    assert ok.mean() > 0.95
+    compare_sequences(cells.cpu().numpy(), n_cells.cpu().numpy(), oc, on, flags)
+    assert np.array_equal(steps.cpu().numpy()[ok], osteps[ok])
+    assert np.abs(rgb.cpu().numpy()[ok] - orgb[ok]).max() <= IMG_TOL
+    assert np.abs(T.cpu().numpy()[ok] - oT[ok]).max() <= IMG_TOL
+    te = t_exit.cpu().numpy()
+    m = np.isfinite(ot) & ok[:, None] & (np.arange(256)[None] < on[:, None])
+    assert np.abs(te[m] - ot[m]).max() <= 1e-5 * max(1.0, np.abs(ot[m]).max())
+
+
+def test_medium_forward_parity_ragged_tiles(medium):
+    sc, osc, o, d, cams = medium
+    scene = api.Scene.from_workload(sc)
+    base = W.default_params()
+    P = gpu_params(base, img_w=203, img_h=121, n_images=2)
+    to, td = to_dev(o, d)
+    rgb, T, steps = api.render_fwd(scene, to, td, P)
+    cells, _, n_cells = api.trace_cells(scene, to, td, P, max_cells=400)
+    assert scene.get_error()[0] == 0
+    orgb, oT, osteps, flags = O.render(osc, o, d, params=oracle_params(base))
+    oc, _, on, _ = O.trace(osc, o, d, max_cells=400, params=oracle_params(base))
+    n_ok, n_flag_diff = compare_sequences(cells.cpu().numpy(), n_cells.cpu().numpy(), oc, on, flags)
+    ok = (flags & O.BAND_FLAGS) == 0
+    assert n_ok > 0.95 * len(o)
+    assert np.abs(rgb.cpu().numpy()[ok] - orgb[ok]).max() <= IMG_TOL
+    assert np.array_equal(steps.cpu().numpy()[ok], osteps[ok])
+
+
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_half_precision_textures(medium, dtype):
+    sc, osc, o, d, cams = medium
+    base = W.default_params()
+    P = gpu_params(base, img_w=203, img_h=121, n_images=2)
+    scene = api.Scene.from_workload(sc, tex_dtype=dtype)
+    to, td = to_dev(o, d)
+    rgb = api.render_fwd(scene, to, td, P)[0].cpu().numpy()
+    # (ii) oracle on the dequantised textures: kernel error only
+    tq = torch.as_tensor(sc.tex).to(torch.float16 if dtype == "f16" else torch.bfloat16).float().numpy()
+    osq = O.OracleScene(sc.sites, sc.sigma, tq, sc.offsets, sc.indices)
+    orgb_q, _, _, flags = O.render(osq, o, d, params=oracle_params(base))
+    ok = (flags & O.BAND_FLAGS) == 0
+    assert np.abs(rgb[ok] - orgb_q[ok]).max() <= IMG_TOL
+    # (i) oracle on the FP32 textures: total error, RMSE <= 2e-3
+    orgb, _, _, _ = O.render(osc, o, d, params=oracle_params(base))
+    rmse = math.sqrt(np.mean((rgb[ok] - orgb[ok]) ** 2))
+    assert rmse <= 2e-3, rmse
+
+
+def test_exactly_representable_f16_texture_is_exact(tiny):
+    wl, osc, o, d = tiny
+    sc = wl.scene
+    tex = np.round(sc.tex * 16) / 16  # k/16 values are exact in FP16 and BF16
+    P = gpu_params(wl.params, img_w=64, img_h=64, n_images=1)
+    to, td = to_dev(o, d)
+    a = api.render_fwd(api.Scene(sc.sites, sc.sigma, tex, sc.offsets, sc.indices, tex_dtype="f32"), to, td, P)[0]
+    b = api.render_fwd(api.Scene(sc.sites, sc.sigma, tex, sc.offsets, sc.indices, tex_dtype="f16"), to, td, P)[0]
+    assert torch.equal(a, b)
+
+
+def test_skip_weight_rule(tiny):
+    wl, osc, o, d = tiny
+    scene = api.Scene.from_workload(wl.scene)
+    P = gpu_params(wl.params, skip_weight=1e-2, img_w=64, img_h=64, n_images=1)
+    to, td = to_dev(o, d)
+    rgb = api.render_fwd(scene, to, td, P)[0].cpu().numpy()
+    orgb, _, _, flags = O.render(osc, o, d, params=oracle_params(wl.params, skip_weight=1e-2))
+    ok = (flags & O.BAND_FLAGS) == 0
+    assert np.abs(rgb[ok] - orgb[ok]).max() <= IMG_TOL
+
+
+# ---------------------------------------------------------------- backward
+
+def test_tiny_backward_parity(tiny):
+    wl, osc, o, d = tiny
+    sc = wl.scene
+    P = gpu_params(wl.params, img_w=64, img_h=64, n_images=1)
+    _, _, _, flags = O.render(osc, o, d, params=oracle_params(wl.params))
+    ok = (flags & O.BAND_FLAGS) == 0
+    Y = W.target_image(len(o), 1)
+    g = np.random.default_rng(5).normal(size=(len(o), 3)) * ok[:, None]  # flagged rays carry no gradient
+    scene = api.Scene.from_workload(sc)
+    to, td, tg = to_dev(o, d, g.astype(np.float32))
+    rgb = api.render_fwd(scene, to, td, P)[0]
+    gs, gsig, gt = api.render_bwd(scene, to, td, P, rgb, tg)
+    assert scene.get_error()[0] == 0
+    ogs, ogsig, ogt = O.render_bwd(osc, o, d, g.astype(np.float32).astype(np.float64),
+                                   params=oracle_params(wl.params))
+    grad_close(gsig.cpu().numpy(), ogsig, "sigma")
+    grad_close(gt.cpu().numpy(), ogt, "tex")
+    grad_close(gs.cpu().numpy(), ogs, "sites")
+    del Y
+
+
+def test_medium_backward_parity(medium):
+    sc, osc, o, d, cams = medium
+    base = W.default_params()
+    P = gpu_params(base, img_w=203, img_h=121, n_images=2)
+    _, _, _, flags = O.render(osc, o, d, params=oracle_params(base))
+    ok = (flags & O.BAND_FLAGS) == 0
+    g = (np.random.default_rng(6).normal(size=(len(o), 3)) * ok[:, None]).astype(np.float32)
+    scene = api.Scene.from_workload(sc)
+    to, td, tg = to_dev(o, d, g)
+    rgb = api.render_fwd(scene, to, td, P)[0]
+    gs, gsig, gt = api.render_bwd(scene, to, td, P, rgb, tg)
+    ogs, ogsig, ogt = O.render_bwd(osc, o, d, g.astype(np.float64), params=oracle_params(base))
+    grad_close(gsig.cpu().numpy(), ogsig, "sigma")
+    grad_close(gt.cpu().numpy(), ogt, "tex")
+    grad_close(gs.cpu().numpy(), ogs, "sites")
+
+
+def test_chunked_gradients_sum(medium):
+    """Rays split into chunks (one per data-parallel replica): the sum of the
+    chunk gradients equals the gradient of all rays at once."""
+    sc, osc, o, d, cams = medium
+    P1 = gpu_params(W.default_params())
+    scene = api.Scene.from_workload(sc)
+    to, td = to_dev(o, d)
+    g = torch.randn(len(o), 3, device=DEV)
+    rgb = api.render_fwd(scene, to, td, P1)[0]
+    full = api.render_bwd(scene, to, td, P1, rgb, g)
+    acc = [torch.zeros_like(x) for x in full]
+    for sl in (slice(0, 9000), slice(9000, 30000), slice(30000, len(o))):
+        part = api.render_bwd(scene, to[sl].contiguous(), td[sl].contiguous(), P1, rgb[sl].contiguous(),
+                              g[sl].contiguous())
+        for a, p in zip(acc, part):
+            a += p
+    for a, f in zip(acc, full):
+        scale = f.abs().max().item()
+        assert (a - f).abs().max().item() <= 1e-4 * scale
+
+
+def test_autograd_function(tiny):
+    wl, osc, o, d = tiny
+    sc = wl.scene
+    P = gpu_params(wl.params, img_w=64, img_h=64, n_images=1)
+    scene = api.Scene.from_workload(sc)
+    sites = torch.tensor(sc.sites, device=DEV, requires_grad=True)
+    sigma = torch.tensor(sc.sigma, device=DEV, requires_grad=True)
+    tex = torch.tensor(sc.tex, device=DEV, requires_grad=True)
+    to, td = to_dev(o, d)
+    Y = torch.as_tensor(W.target_image(len(o), 1), device=DEV)
+    rgb = api.render(sites, sigma, tex, to, td, scene, P)
+    loss = ((rgb - Y) ** 2).mean()
+    loss.backward()
+    gs, gsig, gt = api.render_bwd(scene, to, td, P, rgb.detach(), 2 * (rgb.detach() - Y) / rgb.numel())
+    assert torch.allclose(sites.grad, gs, rtol=1e-5, atol=1e-9)
+    assert torch.allclose(sigma.grad, gsig, rtol=1e-5, atol=1e-9)
+    assert torch.allclose(tex.grad, gt, rtol=1e-5, atol=1e-9)
+
+
+def test_l2_loss_kernel(tiny):
+    wl, osc, o, d = tiny
+    rgb = torch.rand(4096, 3, device=DEV)
+    Y = torch.rand(4096, 3, device=DEV)
+    loss, grad = api.l2_loss(rgb, Y)
+    r64 = (rgb.double() - Y.double())
+    assert abs(loss.item() - (r64 ** 2).mean().item()) < 1e-6
+    assert torch.allclose(grad.double(), 2 * r64 / r64.numel(), rtol=1e-6, atol=1e-12)
+
+
+# ---------------------------------------------------------------- ray generation
+
+@pytest.mark.parametrize("kind", [0, 1, 2, 3])
+def test_raygen_parity(kind):
+    eye = W.orbit_eye(np.zeros(3), 3.0, 67.5, 20.0)
+    kw = {}
+    if kind == 2:
+        kw = dict(rs_velocity=(0.05, -0.02, 0.0))
+    if kind == 3:
+        kw = dict(lens_radius=0.01, focus_dist=3.0, lens_samples=4, seed=4242)
+    cam = W.look_at_camera(kind, 130, 83, eye, np.zeros(3), **kw)
+    o, d, t = api.generate_rays([cam, cam])
+    oo, od, ot = O.raygen(cam)
+    oo, od, ot = np.concatenate([oo, oo]), np.concatenate([od, od]), np.concatenate([ot, ot])
+    assert np.abs(o.cpu().numpy() - oo).max() <= 4e-7 * 3.0
+    assert np.abs(d.cpu().numpy() - od).max() <= 4e-6
+    assert np.abs(t.cpu().numpy() - ot).max() <= 1e-7
+
+
+def test_average_samples():
+    x = torch.rand(40, 3, device=DEV)
+    y = api.average_samples(x, 4)
+    assert torch.allclose(y, x.view(10, 4, 3).mean(1), atol=1e-7)
+    g = torch.rand(10, 3, device=DEV)
+    gx = api.average_samples_bwd(g, 4)
+    assert torch.allclose(gx, g.repeat_interleave(4, 0) / 4, atol=1e-7)
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_empty_and_missing_rays(tiny):
+    wl, osc, o, d = tiny
+    scene = api.Scene.from_workload(wl.scene)
+    P = gpu_params(wl.params)
+    e = torch.empty(0, 3, device=DEV)
+    rgb, T, s = api.render_fwd(scene, e, e, P)
+    assert rgb.shape == (0, 3)
+    # rays pointing away from the clip box: background, T = 1, no steps
+    o2 = torch.tensor([[2.0, 2.0, 2.0]] * 5, device=DEV)
+    d2 = torch.tensor([[1.0, 0.0, 0.0]] * 5, device=DEV)
+    rgb, T, s = api.render_fwd(scene, o2, d2, P)
+    assert torch.all(rgb == 1) and torch.all(T == 1) and torch.all(s == 0)
+
+
+def test_single_site_scene_closed_form():
+    c = np.array([0.2, 0.5, 0.9], np.float32)
+    tex = np.broadcast_to(c, (1, 4, 4, 3)).copy()
+    scene = api.Scene(np.array([[0.1, 0.2, 0.3]], np.float32), np.array([1.7], np.float32), tex,
+                      np.array([0, 0]), np.zeros(0, np.int32))
+    rng = np.random.default_rng(3)
+    o = rng.uniform(-2, 2, size=(64, 3)).astype(np.float32)
+    d = rng.normal(size=(64, 3))
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    P = api.make_params(t_near=0.2, t_far=1.5, T_eps=0.0)
+    rgb = api.render_fwd(scene, *to_dev(o, d), P)[0].cpu().numpy()
+    L = 1.3
+    ref = (1 - np.exp(-1.7 * L)) * c + np.exp(-1.7 * L)
+    assert np.abs(rgb - ref).max() <= 1e-6
+
+
+def test_max_steps_and_capacity_errors(tiny):
+    wl, osc, o, d = tiny
+    scene = api.Scene.from_workload(wl.scene)
+    to, td = to_dev(o, d)
+    api.render_fwd(scene, to, td, gpu_params(wl.params, max_steps=4))
+    assert scene.get_error()[0] == api._vt.VT_ERR_MAX_STEPS
+    api.trace_cells(scene, to, td, gpu_params(wl.params), max_cells=2)
+    assert scene.get_error()[0] == api._vt.VT_ERR_CAPACITY
+    api.render_fwd(scene, to, td, gpu_params(wl.params))
+    assert scene.get_error()[0] == 0
+    bad = td.clone()
+    bad[7] = 0
+    rgb = api.render_fwd(scene, to, bad, gpu_params(wl.params))[0]
+    assert scene.get_error()[0] == api._vt.VT_ERR_INVALID_ARG
+    assert torch.all(rgb[7] == 0)
+
+
+def test_create_rejects_malformed_inputs():
+    sc = W.make_scene("uniform", 300, 4, 9)
+    good = dict(sites=sc.sites, sigma=sc.sigma, tex=sc.tex, adj_offsets=sc.offsets, adj_indices=sc.indices)
+    api.Scene(**good).close()
+
+    def rejects(**kw):
+        args = dict(good)
+        args.update(kw)
+        with pytest.raises(api._vt.VTError) as e:
+            api.Scene(**args)
+        assert e.value.status == api._vt.VT_ERR_INVALID_ARG
+
+    s = sc.sites.copy()
+    s[5, 1] = np.nan
+    rejects(sites=s)
+    g = sc.sigma.copy()
+    g[3] = -1
+    rejects(sigma=g)
+    idx = sc.indices.copy()
+    idx[10] = 300  # out of range
+    rejects(adj_indices=idx)
+    idx = sc.indices.copy()
+    row0 = idx[sc.offsets[0]:sc.offsets[1]]
+    idx[sc.offsets[0]] = 0  # self loop in row 0
+    rejects(adj_indices=idx)
+    idx = sc.indices.copy()
+    j = idx[sc.offsets[0]]
+    idx[sc.offsets[0]] = [k for k in range(1, 300) if k not in row0][0]  # asymmetric
+    rejects(adj_indices=idx)
+    del j
+
+
+def test_scene_update_matches_fresh_scene(tiny):
+    wl, osc, o, d = tiny
+    sc = wl.scene
+    P = gpu_params(wl.params, img_w=64, img_h=64, n_images=1)
+    to, td = to_dev(o, d)
+    scene = api.Scene.from_workload(sc)
+    rng = np.random.default_rng(4)
+    sites2 = (sc.sites + rng.normal(0, 1e-4, size=sc.sites.shape)).astype(np.float32)
+    sig2 = (sc.sigma * 1.5).astype(np.float32)
+    tex2 = rng.uniform(0, 1, size=sc.tex.shape).astype(np.float32)
+    scene.update(sites2, sig2, tex2)
+    a = api.render_fwd(scene, to, td, P)[0]
+    fresh = api.Scene(sites2, sig2, tex2, sc.offsets, sc.indices)
+    b = api.render_fwd(fresh, to, td, P)[0]
+    assert torch.equal(a, b)

@@ -1,0 +1,104 @@
+"""Host-side checks that need no GPU: the C-ABI library loads and exports every
+symbol include/vt.h declares, host argument validation, workload inputs."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "vt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(vt_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def vt():
+    from paper_2608_17682_gb300 import build
+    build.build()
+    from paper_2608_17682_gb300 import _vt
+    return _vt
+
+
+def test_header_matches_binding_list(vt):
+    assert _declared() == sorted(vt.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(vt):
+    out = subprocess.run(["nm", "-D", "--defined-only", vt.LIB_PATH], capture_output=True, text=True).stdout
+    syms = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = [s for s in _declared() if s not in syms]
+    assert not missing, missing
+    for s in _declared():
+        assert hasattr(vt.lib, s)
+
+
+def test_status_strings_and_defaults(vt):
+    assert vt.status_str(0) == "VT_OK"
+    assert vt.status_str(4) == "VT_ERR_MAX_STEPS"
+    p = vt.vt_render_params_default()
+    assert p.t_near == 0 and p.t_far == 20 and abs(p.T_eps - 1e-4) < 1e-10 and list(p.bg) == [1, 1, 1]
+    assert p.skip_weight == 0 and p.img_w == 0 and p.max_steps == 0
+
+
+def test_host_argument_validation(vt):
+    import ctypes as C
+    out = C.c_void_p(123)
+    assert vt.lib.vt_scene_create(None, None, C.byref(out)) == vt.VT_ERR_INVALID_ARG
+    assert out.value is None
+    d = vt.vt_scene_desc(0, 4, 0, 0, 0, 0, 0, 0)
+    assert vt.lib.vt_scene_create(C.byref(d), None, C.byref(out)) == vt.VT_ERR_INVALID_ARG
+    d = vt.vt_scene_desc(10, 1, 0, 8, 8, 8, 8, 8)  # tex_res < 2
+    assert vt.lib.vt_scene_create(C.byref(d), None, C.byref(out)) == vt.VT_ERR_INVALID_ARG
+    d = vt.vt_scene_desc(10, 4, 7, 8, 8, 8, 8, 8)  # bad dtype
+    assert vt.lib.vt_scene_create(C.byref(d), None, C.byref(out)) == vt.VT_ERR_INVALID_ARG
+    cam = vt.vt_camera()
+    cam.kind, cam.w, cam.h = 3, 4, 4
+    cam.fwd[:] = [1, 0, 0]
+    cam.up[:] = [0, 0, 1]
+    cam.lens_samples = 3  # not a square
+    arr = (vt.vt_camera * 1)(cam)
+    assert vt.lib.vt_generate_rays(arr, 1, C.c_void_p(8), C.c_void_p(8), None, None) == vt.VT_ERR_INVALID_ARG
+    cam.lens_samples = 4
+    assert vt.vt_camera_n_rays(cam) == 64
+    assert vt.lib.vt_render_fwd(None, 1, None, None, None, None, None, None, None, None) == vt.VT_ERR_INVALID_ARG
+    assert vt.lib.vt_l2_loss(-1, None, None, None, None, None) == vt.VT_ERR_INVALID_ARG
+    assert vt.lib.vt_average_samples(4, 0, None, None, None) == vt.VT_ERR_INVALID_ARG
+
+
+def test_workload_csr_is_a_valid_delaunay_graph():
+    from paper_2608_17682_gb300 import workloads as W
+    sc = W.make_scene("uniform", 3000, 4, 5)
+    off, idx = sc.offsets, sc.indices
+    n = sc.n
+    assert off[0] == 0 and off[-1] == len(idx) and np.all(np.diff(off) > 0)
+    rows = np.repeat(np.arange(n), np.diff(off))
+    assert np.all(idx != rows) and idx.min() >= 0 and idx.max() < n
+    e = set(zip(rows.tolist(), idx.tolist()))
+    assert all((j, i) in e for i, j in e)
+    assert 13 < len(idx) / n < 17  # mean Delaunay degree of a random 3-D point set is about 15.5
+
+
+def test_surface_workload_recipe():
+    from paper_2608_17682_gb300 import workloads as W
+    rng = np.random.default_rng(0)
+    pts, surf = W.surface_sites(20000, rng)
+    r = np.linalg.norm(pts.astype(np.float64), axis=1)
+    assert abs(surf.mean() - 0.7) < 1e-3
+    shell = r > 3.9
+    assert abs(shell.mean() - 0.1) < 1e-3 and r[shell].max() <= 8.0 + 1e-5
+    inner = ~surf & ~shell
+    assert np.all(np.abs(pts[inner]) <= 1.0)
+
+
+def test_camera_set_of_mixed_workload():
+    from paper_2608_17682_gb300 import workloads as W
+    cams = W.workload_cameras("mixed3m")
+    assert [c.kind for c in cams] == [0] * 4 + [1] * 4 + [2] * 4 + [3] * 4
+    assert sum(c.n_rays for c in cams) == 29_818_880
+    cams = W.workload_cameras("prec3m")
+    assert sum(c.n_rays for c in cams) == 4 * 1280 * 832
