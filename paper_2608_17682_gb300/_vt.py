@@ -12,7 +12,7 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libvt.so")
+LIB_PATH = os.environ.get("VT_LIB_PATH") or os.path.join(HERE, "libvt.so")
 
 VT_OK, VT_ERR_INVALID_ARG, VT_ERR_CUDA, VT_ERR_OOM, VT_ERR_MAX_STEPS, VT_ERR_CAPACITY, VT_ERR_UNSUPPORTED = range(7)
 VT_F32, VT_F16, VT_BF16 = 0, 1, 2

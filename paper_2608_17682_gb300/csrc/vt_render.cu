@@ -28,6 +28,16 @@ namespace {
 
 enum Mode { FWD = 0, BWD = 1, TRACE = 2 };
 
+// minimum resident 256-thread blocks per SM requested for the walk kernel
+#ifndef VT_WALK_MINB
+#define VT_WALK_MINB 2
+#endif
+// 1: issue a cell's texel loads before its exit search (latency overlapped,
+// more live registers); 0: after it
+#ifndef VT_TEX_EARLY
+#define VT_TEX_EARLY 1
+#endif
+
 struct Scene {
   const float4* __restrict__ site;
   const int4* __restrict__ meta;
@@ -101,20 +111,50 @@ __device__ __forceinline__ void ff_add(float& th, float& tl, float x) {
 __device__ __forceinline__ bool ff_gt(float th, float tl, float x) { return th > x || (th == x && tl > 0.f); }
 __device__ __forceinline__ bool ff_ge(float th, float tl, float x) { return th > x || (th == x && tl >= 0.f); }
 
-__device__ __forceinline__ float4 load_texel(const void* tex, int64_t e, int DT) {
-  if (DT == VT_F32) return __ldg(reinterpret_cast<const float4*>(tex) + e);
-  uint2 u = __ldg(reinterpret_cast<const uint2*>(tex) + e);
-  if (DT == VT_F16) {
-    __half2 a = *reinterpret_cast<__half2*>(&u.x), b = *reinterpret_cast<__half2*>(&u.y);
-    float2 fa = __half22float2(a), fb = __half22float2(b);
-    return make_float4(fa.x, fa.y, fb.x, fb.y);
-  }
-  return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u), __uint_as_float(u.y << 16),
-                     __uint_as_float(u.y & 0xffff0000u));
+// Raw texel (RGBA): FP32 as float4, FP16/BF16 as 4 x 16 bits in a uint2 (kept
+// packed until use to save registers).
+template <int DT>
+struct TexRaw {
+  uint2 v;
+};
+template <>
+struct TexRaw<VT_F32> {
+  float4 v;
+};
+
+template <int DT>
+__device__ __forceinline__ TexRaw<DT> load_texel(const void* tex, int64_t e) {
+  TexRaw<DT> t;
+  if constexpr (DT == VT_F32)
+    t.v = __ldg(reinterpret_cast<const float4*>(tex) + e);
+  else
+    t.v = __ldg(reinterpret_cast<const uint2*>(tex) + e);
+  return t;
 }
 
-// Octahedral map (Sec. 5.1) + bilinear taps, texel index y*R + x, clamp to edge.
-__device__ __forceinline__ void taps_for(float3 d, int R, int tap[4], float tw[4]) {
+template <int DT>
+__device__ __forceinline__ float3 texel_rgb(const TexRaw<DT>& t) {
+  if constexpr (DT == VT_F32) {
+    return make_float3(t.v.x, t.v.y, t.v.z);
+  } else if constexpr (DT == VT_F16) {
+    uint2 u = t.v;
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+    return make_float3(a.x, a.y, __half2float(*reinterpret_cast<const __half*>(&u.y)));
+  } else {
+    return make_float3(__uint_as_float(t.v.x << 16), __uint_as_float(t.v.x & 0xffff0000u),
+                       __uint_as_float(t.v.y << 16));
+  }
+}
+
+// Octahedral map (Sec. 5.1) + bilinear taps, texel index y*R + x, clamp to
+// edge. Returned compactly: base texel, x / y steps (0 at the clamped edge)
+// and the fractional offsets; taps are base, base+sx, base+sy, base+sx+sy.
+struct Taps {
+  int base, sx, sy;
+  float fx, fy;
+};
+
+__device__ __forceinline__ Taps taps_for(float3 d, int R) {
   float l1 = __fadd_rn(__fadd_rn(fabsf(d.x), fabsf(d.y)), fabsf(d.z));
   float qx = __fdiv_rn(d.x, l1), qy = __fdiv_rn(d.y, l1);
   float u, v;
@@ -130,16 +170,57 @@ __device__ __forceinline__ void taps_for(float3 d, int R, int tap[4], float tw[4
   x = fminf(fmaxf(x, 0.f), (float)(R - 1));
   y = fminf(fmaxf(y, 0.f), (float)(R - 1));
   int x0 = min((int)floorf(x), R - 1), y0 = min((int)floorf(y), R - 1);
-  int x1 = min(x0 + 1, R - 1), y1 = min(y0 + 1, R - 1);
-  float fx = __fsub_rn(x, (float)x0), fy = __fsub_rn(y, (float)y0);
-  tap[0] = y0 * R + x0;
-  tap[1] = y0 * R + x1;
-  tap[2] = y1 * R + x0;
-  tap[3] = y1 * R + x1;
-  tw[0] = __fmul_rn(__fsub_rn(1.f, fx), __fsub_rn(1.f, fy));
-  tw[1] = __fmul_rn(fx, __fsub_rn(1.f, fy));
-  tw[2] = __fmul_rn(__fsub_rn(1.f, fx), fy);
-  tw[3] = __fmul_rn(fx, fy);
+  Taps t;
+  t.base = y0 * R + x0;
+  t.sx = x0 + 1 < R ? 1 : 0;
+  t.sy = y0 + 1 < R ? R : 0;
+  t.fx = __fsub_rn(x, (float)x0);
+  t.fy = __fsub_rn(y, (float)y0);
+  return t;
+}
+
+__device__ __forceinline__ void tap_weights(const Taps& t, float w[4]) {
+  const float gx = __fsub_rn(1.f, t.fx), gy = __fsub_rn(1.f, t.fy);
+  w[0] = __fmul_rn(gx, gy);
+  w[1] = __fmul_rn(t.fx, gy);
+  w[2] = __fmul_rn(gx, t.fy);
+  w[3] = __fmul_rn(t.fx, t.fy);
+}
+
+// Exact n.d for n = sj - si (FP32 inputs): n is split into rounded part and
+// rounding error (TwoSum), products are split by FMA (TwoProd) and summed with
+// compensation -- accurate to about FP32 rounding of the exact value even for
+// grazing crossings, where the plain FP32 dot product loses all digits.
+__device__ __forceinline__ float exact_nd(float3 si, float3 sj, float3 d) {
+  float h0, l0, h1, l1, h2, l2;
+  two_sum(sj.x, -si.x, h0, l0);
+  two_sum(sj.y, -si.y, h1, l1);
+  two_sum(sj.z, -si.z, h2, l2);
+  const float p0 = __fmul_rn(h0, d.x), p1 = __fmul_rn(h1, d.y), p2 = __fmul_rn(h2, d.z);
+  float e = __fmaf_rn(h0, d.x, -p0);
+  e = __fadd_rn(e, __fmaf_rn(h1, d.y, -p1));
+  e = __fadd_rn(e, __fmaf_rn(h2, d.z, -p2));
+  e = __fmaf_rn(l0, d.x, __fmaf_rn(l1, d.y, __fmaf_rn(l2, d.z, e)));
+  float s, c1, c2;
+  two_sum(p0, p1, s, c1);
+  float s2;
+  two_sum(s, p2, s2, c2);
+  return __fadd_rn(s2, __fadd_rn(__fadd_rn(c1, c2), e));
+}
+
+// FP64 re-evaluation of a grazing plane from the FP32 inputs: returns false if
+// the plane is not crossed forward, else the exact-in-FP64 step dt (as num/1).
+__device__ __noinline__ bool grazing_fp64(float4 q, float3 si, float3 o, float3 d, float th, float tl, float* dt) {
+  const double t64 = (double)th + (double)tl;
+  const double n0 = (double)q.x - (double)si.x, n1 = (double)q.y - (double)si.y, n2 = (double)q.z - (double)si.z;
+  const double den64 = n0 * (double)d.x + n1 * (double)d.y + n2 * (double)d.z;
+  if (!(den64 > 0.0)) return false;
+  const double r0 = (double)si.x - ((double)o.x + t64 * (double)d.x),
+               r1 = (double)si.y - ((double)o.y + t64 * (double)d.y),
+               r2 = (double)si.z - ((double)o.z + t64 * (double)d.z);
+  const double num64 = n0 * r0 + n1 * r1 + n2 * r2 + 0.5 * (n0 * n0 + n1 * n1 + n2 * n2);
+  *dt = (float)(num64 / den64);
+  return true;
 }
 
 // Greedy descent on the Delaunay graph to the site nearest q, ordering sites
@@ -222,10 +303,11 @@ __device__ __forceinline__ int64_t ray_of_thread(const RP& P, int64_t tid) {
 
 // ---------------------------------------------------------------- the walk
 template <int MODE, int DT>
-__global__ void __launch_bounds__(256) k_walk(Scene S, RP P, const float* __restrict__ O, const float* __restrict__ D,
-                                              const int32_t* __restrict__ anchor_cell, float* __restrict__ rgb_out,
-                                              float* __restrict__ T_out, int32_t* __restrict__ steps_out, Grad G,
-                                              Trace TR) {
+__global__ void __launch_bounds__(256, VT_WALK_MINB) k_walk(Scene S, RP P, const float* __restrict__ O,
+                                                            const float* __restrict__ D,
+                                                            const int32_t* __restrict__ anchor_cell,
+                                                            float* __restrict__ rgb_out, float* __restrict__ T_out,
+                                                            int32_t* __restrict__ steps_out, Grad G, Trace TR) {
   const int64_t ray = ray_of_thread(P, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
   if (ray < 0) return;
   const float3 o = make_float3(O[3 * ray], O[3 * ray + 1], O[3 * ray + 2]);
@@ -234,7 +316,7 @@ __global__ void __launch_bounds__(256) k_walk(Scene S, RP P, const float* __rest
   float C0 = 0.f, C1 = 0.f, C2 = 0.f;
   float T = 1.f;
   int k = 0;
-  bool bad = !(dd > 0.f) || !isfinite(dd) || !isfinite(o.x) || !isfinite(o.y) || !isfinite(o.z);
+  const bool bad = !(dd > 0.f) || !isfinite(dd) || !isfinite(o.x) || !isfinite(o.y) || !isfinite(o.z);
   // clip [t_near, t_far] to the optional box (slab test)
   float t0 = P.t_near, t1 = P.t_far;
   if (P.clip && !bad) {
@@ -251,38 +333,37 @@ __global__ void __launch_bounds__(256) k_walk(Scene S, RP P, const float* __rest
       }
     }
   }
-  // BWD inputs
-  float g0 = 0.f, g1 = 0.f, g2 = 0.f, Co0 = 0.f, Co1 = 0.f, Co2 = 0.f;
-  if (MODE == BWD) {
-    g0 = G.grad[3 * ray];
-    g1 = G.grad[3 * ray + 1];
-    g2 = G.grad[3 * ray + 2];
-    Co0 = G.rgb[3 * ray];
-    Co1 = G.rgb[3 * ray + 1];
-    Co2 = G.rgb[3 * ray + 2];
-  }
   if (bad) {
     atomicOr(S.err, (unsigned long long)VT_EBIT_BAD_RAY);
   } else if (t1 > t0) {
-    int tap[4];
-    float tw[4];
-    taps_for(d, S.R, tap, tw);
+    const Taps tp = taps_for(d, S.R);
     const float G2dd = __fmul_rn(1e-12f, dd);  // grazing: (n.d)^2 <= 1e-12 |n|^2 |d|^2
-    const double3 o64 = make_double3(o.x, o.y, o.z), d64 = make_double3(d.x, d.y, d.z);
+    // BWD: g = dL/dC, S = C_out - (prefix of w c) = suffix S_k after step k
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f, S0 = 0.f, S1 = 0.f, S2 = 0.f;
+    if (MODE == BWD) {
+      g0 = G.grad[3 * ray];
+      g1 = G.grad[3 * ray + 1];
+      g2 = G.grad[3 * ray + 2];
+      S0 = G.rgb[3 * ray];
+      S1 = G.rgb[3 * ray + 1];
+      S2 = G.rgb[3 * ray + 2];
+    }
     // start cell: greedy walk from this ray's anchor cell to the origin
     bool ok = true;
     int cell = greedy_nearest(S, anchor_cell[ray / P.anchor_stride], o, P.max_steps, ok);
     if (!ok) atomicOr(S.err, (unsigned long long)VT_EBIT_MAX_STEPS);
-    float4 s4 = __ldg(S.site + cell);
-    float3 si = make_float3(s4.x, s4.y, s4.z);
+    float3 si;
+    {
+      const float4 s4 = __ldg(S.site + cell);
+      si = make_float3(s4.x, s4.y, s4.z);
+    }
     float th = 0.f, tl = 0.f;  // entry parameter of the current cell (float-float)
-    float A0 = 0.f, A1 = 0.f, A2 = 0.f;  // BWD: prefix of w c (inclusive)
-    // BWD carry: previous cell
+    // BWD carry: previous cell, its sigma * dL/dtau, site gradient so far,
+    // dL/dsigma, its site position; whether the entry crossing is differentiable
     int pc = -1;
-    float p_sig = 0.f, p_dtau = 0.f, p_gsig = 0.f;
+    float p_sdtau = 0.f, p_gsig = 0.f;
     float3 p_gs = make_float3(0.f, 0.f, 0.f), p_s = si;
     bool cross_valid = false;
-    float3 cross_n = make_float3(0.f, 0.f, 0.f);
     for (;;) {
       if (k >= P.max_steps) {
         atomicOr(S.err, (unsigned long long)VT_EBIT_MAX_STEPS);
@@ -291,17 +372,20 @@ __global__ void __launch_bounds__(256) k_walk(Scene S, RP P, const float* __rest
       const int4 m = __ldg(S.meta + cell);
       const float sig = __int_as_float(m.z);
       // texels of this cell (independent of the exit search)
-      float4 tx[4];
-      if (MODE != TRACE) {
-        const int64_t base = (int64_t)cell * S.RR;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) tx[q] = load_texel(S.tex, base + tap[q], DT);
+      TexRaw<DT> tx0, tx1, tx2, tx3;
+      const int64_t tb0 = (int64_t)cell * S.RR + tp.base;
+      if (MODE != TRACE && VT_TEX_EARLY) {
+        tx0 = load_texel<DT>(S.tex, tb0);
+        tx1 = load_texel<DT>(S.tex, tb0 + tp.sx);
+        tx2 = load_texel<DT>(S.tex, tb0 + tp.sy);
+        tx3 = load_texel<DT>(S.tex, tb0 + tp.sx + tp.sy);
       }
       const float3 r = rel_pos(si, o, d, th, tl);
       // ---- exit search over the Delaunay neighbours
       float bn = 1.f, bd = 0.f;  // best dt = bn / bd (bd == 0: none yet)
       int bj = -1;
       float3 bq = si;
+#pragma unroll 2
       for (int p = m.x; p < m.y; ++p) {
         const float4 q = __ldg(S.nbr + p);
         const float nx = __fsub_rn(q.x, si.x), ny = __fsub_rn(q.y, si.y), nz = __fsub_rn(q.z, si.z);
@@ -311,15 +395,7 @@ __global__ void __launch_bounds__(256) k_walk(Scene S, RP P, const float* __rest
         if (__fmul_rn(den, den) <= __fmul_rn(G2dd, nn)) {
           // grazing plane: FP64 recheck from the FP32 inputs
           atomicAdd(S.err + 1, 1ull);
-          const double t64 = (double)th + (double)tl;
-          const double n0 = (double)q.x - (double)si.x, n1 = (double)q.y - (double)si.y,
-                       n2 = (double)q.z - (double)si.z;
-          const double den64 = n0 * d64.x + n1 * d64.y + n2 * d64.z;
-          if (!(den64 > 0.0)) continue;
-          const double r0 = (double)si.x - (o64.x + t64 * d64.x), r1 = (double)si.y - (o64.y + t64 * d64.y),
-                       r2 = (double)si.z - (o64.z + t64 * d64.z);
-          const double num64 = n0 * r0 + n1 * r1 + n2 * r2 + 0.5 * (n0 * n0 + n1 * n1 + n2 * n2);
-          num = (float)(num64 / den64);
+          if (!grazing_fp64(q, si, o, d, th, tl, &num)) continue;
           den = 1.f;
         } else if (!(den > 0.f)) {
           continue;
@@ -332,6 +408,12 @@ __global__ void __launch_bounds__(256) k_walk(Scene S, RP P, const float* __rest
         }
       }
       ++k;
+      if (MODE != TRACE && !VT_TEX_EARLY) {
+        tx0 = load_texel<DT>(S.tex, tb0);
+        tx1 = load_texel<DT>(S.tex, tb0 + tp.sx);
+        tx2 = load_texel<DT>(S.tex, tb0 + tp.sy);
+        tx3 = load_texel<DT>(S.tex, tb0 + tp.sx + tp.sy);
+      }
       const float dt = bj >= 0 ? __fdiv_rn(bn, bd) : INFINITY;
       float eh = th, el = tl;  // exit parameter
       if (bj >= 0)
@@ -360,6 +442,7 @@ __global__ void __launch_bounds__(256) k_walk(Scene S, RP P, const float* __rest
       bool stop = false;
       float dtau = 0.f, w = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
       bool coloured = false;
+      float tw[4];
       if (delta > 0.f) {
         const float e = expf(-__fmul_rn(sig, delta));
         const float alpha = __fsub_rn(1.f, e);
@@ -367,67 +450,69 @@ __global__ void __launch_bounds__(256) k_walk(Scene S, RP P, const float* __rest
         const float Tn = __fmul_rn(T, e);
         if (MODE != TRACE && (!(P.skip > 0.f) || w >= P.skip)) {
           coloured = true;
-          c0 = __fmaf_rn(tw[3], tx[3].x, __fmaf_rn(tw[2], tx[2].x, __fmaf_rn(tw[1], tx[1].x, __fmul_rn(tw[0], tx[0].x))));
-          c1 = __fmaf_rn(tw[3], tx[3].y, __fmaf_rn(tw[2], tx[2].y, __fmaf_rn(tw[1], tx[1].y, __fmul_rn(tw[0], tx[0].y))));
-          c2 = __fmaf_rn(tw[3], tx[3].z, __fmaf_rn(tw[2], tx[2].z, __fmaf_rn(tw[1], tx[1].z, __fmul_rn(tw[0], tx[0].z))));
+          tap_weights(tp, tw);
+          const float3 a0 = texel_rgb<DT>(tx0), a1 = texel_rgb<DT>(tx1), a2 = texel_rgb<DT>(tx2),
+                       a3 = texel_rgb<DT>(tx3);
+          c0 = __fmaf_rn(tw[3], a3.x, __fmaf_rn(tw[2], a2.x, __fmaf_rn(tw[1], a1.x, __fmul_rn(tw[0], a0.x))));
+          c1 = __fmaf_rn(tw[3], a3.y, __fmaf_rn(tw[2], a2.y, __fmaf_rn(tw[1], a1.y, __fmul_rn(tw[0], a0.y))));
+          c2 = __fmaf_rn(tw[3], a3.z, __fmaf_rn(tw[2], a2.z, __fmaf_rn(tw[1], a1.z, __fmul_rn(tw[0], a0.z))));
           if (MODE == FWD) {
             C0 = __fmaf_rn(w, c0, C0);
             C1 = __fmaf_rn(w, c1, C1);
             C2 = __fmaf_rn(w, c2, C2);
           } else {
-            A0 = __fmaf_rn(w, c0, A0);
-            A1 = __fmaf_rn(w, c1, A1);
-            A2 = __fmaf_rn(w, c2, A2);
+            S0 = __fsub_rn(S0, __fmul_rn(w, c0));
+            S1 = __fsub_rn(S1, __fmul_rn(w, c1));
+            S2 = __fsub_rn(S2, __fmul_rn(w, c2));
           }
         }
         if (MODE == BWD) {
-          // dL/dtau_k = g . (T_{k+1} c_k - S_k),  S_k = C_out - A_k
-          dtau = g0 * (Tn * c0 - (Co0 - A0)) + g1 * (Tn * c1 - (Co1 - A1)) + g2 * (Tn * c2 - (Co2 - A2));
+          // dL/dtau_k = g . (T_{k+1} c_k - S_k)
+          dtau = g0 * (Tn * c0 - S0) + g1 * (Tn * c1 - S1) + g2 * (Tn * c2 - S2);
         }
         T = Tn;
         if (T < P.T_eps) stop = true;
       }
       if (MODE == BWD) {
-        // crossing between the previous cell and this one (entry face)
+        // crossing between the previous cell and this one (entry face):
+        // dL/dt_b = sigma_prev dtau_prev - sigma dtau; x_b - s_prev = n - r, s_cur - x_b = r
         float3 gs = make_float3(0.f, 0.f, 0.f);
         if (pc >= 0 && cross_valid) {
-          const float nd = __fmaf_rn(cross_n.x, d.x, __fmaf_rn(cross_n.y, d.y, cross_n.z * d.z));
-          const float dtb = (p_sig * p_dtau - sig * dtau) / nd;
-          // x_b - s_prev = n - r ; s_cur - x_b = r
-          p_gs.x += dtb * (cross_n.x - r.x);
-          p_gs.y += dtb * (cross_n.y - r.y);
-          p_gs.z += dtb * (cross_n.z - r.z);
+          const float nd = exact_nd(p_s, si, d);
+          const float dtb = (p_sdtau - sig * dtau) / nd;
+          const float nx = __fsub_rn(si.x, p_s.x), ny = __fsub_rn(si.y, p_s.y), nz = __fsub_rn(si.z, p_s.z);
+          p_gs.x += dtb * (nx - r.x);
+          p_gs.y += dtb * (ny - r.y);
+          p_gs.z += dtb * (nz - r.z);
           gs = make_float3(dtb * r.x, dtb * r.y, dtb * r.z);
         }
         if (pc >= 0 && (p_gs.x != 0.f || p_gs.y != 0.f || p_gs.z != 0.f || p_gsig != 0.f))
           atomicAdd(G.g_cell + pc, make_float4(p_gs.x, p_gs.y, p_gs.z, p_gsig));
         if (coloured && w > 0.f) {
-          const int64_t base = (int64_t)cell * S.RR;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float ww = w * tw[q];
-            if (ww != 0.f) atomicAdd(G.g_tex + base + tap[q], make_float4(g0 * ww, g1 * ww, g2 * ww, 0.f));
-          }
+          const int64_t b0 = tb0;
+          const float ww0 = w * tw[0], ww1 = w * tw[1], ww2 = w * tw[2], ww3 = w * tw[3];
+          if (ww0 != 0.f) atomicAdd(G.g_tex + b0, make_float4(g0 * ww0, g1 * ww0, g2 * ww0, 0.f));
+          if (ww1 != 0.f) atomicAdd(G.g_tex + b0 + tp.sx, make_float4(g0 * ww1, g1 * ww1, g2 * ww1, 0.f));
+          if (ww2 != 0.f) atomicAdd(G.g_tex + b0 + tp.sy, make_float4(g0 * ww2, g1 * ww2, g2 * ww2, 0.f));
+          if (ww3 != 0.f) atomicAdd(G.g_tex + b0 + tp.sx + tp.sy, make_float4(g0 * ww3, g1 * ww3, g2 * ww3, 0.f));
         }
         pc = cell;
-        p_sig = sig;
-        p_dtau = dtau;
+        p_sdtau = sig * dtau;
         p_gsig = dtau * delta;
         p_gs = gs;
         p_s = si;
         // will the crossing at this cell's exit be differentiable?
         cross_valid = (bj >= 0) && !exit_beyond && ff_gt(eh, el, t0);
-        if (bj >= 0) cross_n = make_float3(__fsub_rn(bq.x, si.x), __fsub_rn(bq.y, si.y), __fsub_rn(bq.z, si.z));
         if (stop && cross_valid) {
           // terminated inside the extent: the exit plane still moves delta_K
           const float3 re = rel_pos(si, o, d, eh, el);  // s_K - x_out
-          const float nd = __fmaf_rn(cross_n.x, d.x, __fmaf_rn(cross_n.y, d.y, cross_n.z * d.z));
-          const float dtb = (p_sig * p_dtau) / nd;
+          const float nd = exact_nd(si, bq, d);
+          const float dtb = p_sdtau / nd;
+          const float nx = __fsub_rn(bq.x, si.x), ny = __fsub_rn(bq.y, si.y), nz = __fsub_rn(bq.z, si.z);
           p_gs.x -= dtb * re.x;
           p_gs.y -= dtb * re.y;
           p_gs.z -= dtb * re.z;
-          atomicAdd(G.g_cell + bj,
-                    make_float4(dtb * (re.x + cross_n.x), dtb * (re.y + cross_n.y), dtb * (re.z + cross_n.z), 0.f));
+          atomicAdd(G.g_cell + bj, make_float4(dtb * (re.x + nx), dtb * (re.y + ny), dtb * (re.z + nz), 0.f));
         }
       }
       if (stop || exit_beyond) break;
@@ -438,7 +523,6 @@ __global__ void __launch_bounds__(256) k_walk(Scene S, RP P, const float* __rest
     }
     if (MODE == BWD && pc >= 0 && (p_gs.x != 0.f || p_gs.y != 0.f || p_gs.z != 0.f || p_gsig != 0.f))
       atomicAdd(G.g_cell + pc, make_float4(p_gs.x, p_gs.y, p_gs.z, p_gsig));
-    (void)p_s;
     C0 = __fmaf_rn(T, P.bg.x, C0);
     C1 = __fmaf_rn(T, P.bg.y, C1);
     C2 = __fmaf_rn(T, P.bg.z, C2);

@@ -23,7 +23,10 @@ Seeds: scene 1000+k, camera jitter 2000+k, target image 3000+k, lens samples
 """
 from __future__ import annotations
 
+import hashlib
 import math
+import os
+import tempfile
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -124,18 +127,45 @@ def textures(n: int, R: int, rng: np.random.Generator) -> np.ndarray:
 # Delaunay adjacency (host, scipy / Qhull)
 
 
-def delaunay_csr(sites: np.ndarray):
+def _cache_dir():
+    return os.environ.get("VT_CACHE_DIR", os.path.join(tempfile.gettempdir(), "vt_delaunay_cache"))
+
+
+def delaunay_csr(sites: np.ndarray, cache: bool = True):
     """CSR Delaunay adjacency of the sites: offsets int64 [n+1], indices int32.
 
     Qhull runs on the float64 promotion of the FP32 sites. Raises if Qhull
-    left any site out of the triangulation (duplicates / coplanar points)."""
+    left any site out of the triangulation (duplicates / coplanar points).
+    Results for more than 100k sites are cached on local disk, keyed by a hash
+    of the site array, so that a test run and a benchmark on the same machine
+    triangulate a large scene once."""
     from scipy.spatial import Delaunay
 
+    sites = np.ascontiguousarray(sites, dtype=np.float32)
+    path = None
+    if cache and len(sites) > 100_000:
+        key = hashlib.sha1(sites.tobytes()).hexdigest()[:20]
+        path = os.path.join(_cache_dir(), f"{key}_{len(sites)}.npz")
+        if os.path.exists(path):
+            try:
+                z = np.load(path)
+                return z["offsets"], z["indices"]
+            except Exception:
+                pass
     tri = Delaunay(sites.astype(np.float64))
     if len(tri.coplanar):
         raise ValueError(f"{len(tri.coplanar)} sites left out of the Delaunay triangulation")
     indptr, indices = tri.vertex_neighbor_vertices
-    return indptr.astype(np.int64), indices.astype(np.int32)
+    off, idx = indptr.astype(np.int64), indices.astype(np.int32)
+    if path:
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            tmp = path + f".{os.getpid()}.npz"
+            np.savez(tmp, offsets=off, indices=idx)
+            os.replace(tmp, path)
+        except OSError:
+            pass
+    return off, idx
 
 
 # --------------------------------------------------------------------------
@@ -208,6 +238,33 @@ def frustum_rays(eye, target, w, h, rng: np.random.Generator, fov_y=math.radians
     # re-normalise after rounding so |d| is 1 to FP32 precision
     d = (d / np.linalg.norm(d.astype(np.float64), axis=1, keepdims=True)).astype(np.float32)
     return np.ascontiguousarray(o.reshape(-1, 3).astype(np.float32)), np.ascontiguousarray(d)
+
+
+def wide_rays(eye, target, n, rng: np.random.Generator, half_angle=math.radians(107.0), origin_radius=0.0,
+              up=(0.0, 0.0, 1.0)):
+    """n rays with directions uniform over the spherical cap of the given
+    half-angle around eye->target, origins uniform on a disk of origin_radius
+    around eye (perpendicular to the axis). Rays are ordered by a coarse
+    (azimuth, polar) grid cell so that consecutive rays are close, and are
+    returned as float32 o, d of shape [n,3] (d unit length)."""
+    eye = np.asarray(eye, dtype=np.float64)
+    f = np.asarray(target, dtype=np.float64) - eye
+    f /= np.linalg.norm(f)
+    r = np.cross(f, up)
+    r /= np.linalg.norm(r)
+    u = np.cross(r, f)
+    z = rng.uniform(math.cos(half_angle), 1.0, size=n)
+    phi = rng.uniform(0.0, 2 * math.pi, size=n)
+    st = np.sqrt(np.maximum(0.0, 1 - z * z))
+    d = z[:, None] * f + (st * np.cos(phi))[:, None] * r + (st * np.sin(phi))[:, None] * u
+    rad = origin_radius * np.sqrt(rng.uniform(0, 1, size=n))
+    ang = rng.uniform(0, 2 * math.pi, size=n)
+    o = eye + (rad * np.cos(ang))[:, None] * r + (rad * np.sin(ang))[:, None] * u
+    order = np.lexsort((z, np.floor(phi / (2 * math.pi) * 64), np.floor((1 - z) * 32)))
+    o, d = o[order], d[order]
+    d = d.astype(np.float32)
+    d = (d / np.linalg.norm(d.astype(np.float64), axis=1, keepdims=True)).astype(np.float32)
+    return np.ascontiguousarray(o.astype(np.float32)), np.ascontiguousarray(d)
 
 
 # --------------------------------------------------------------------------

@@ -386,3 +386,32 @@ def test_scene_update_matches_fresh_scene(tiny):
     fresh = api.Scene(sites2, sig2, tex2, sc.offsets, sc.indices)
     b = api.render_fwd(fresh, to, td, P)[0]
     assert torch.equal(a, b)
+
+
+def test_wide_angle_moving_origin_rays(medium):
+    """Rays shaped like the mixed-camera workload: directions up to 107 deg
+    off-axis (fisheye corners) and origins spread over a 0.05 disk (lens /
+    rolling-shutter motion), 1-D layout, uneven lengths."""
+    sc, osc, o_, d_, cams = medium
+    o, d = W.wide_rays(W.orbit_eye(np.zeros(3), 3.0, 100.0, 20.0), np.zeros(3), 20000,
+                       np.random.default_rng(79), origin_radius=0.05)
+    base = W.default_params()
+    scene = api.Scene.from_workload(sc, tex_dtype="f16")
+    to, td = to_dev(o, d)
+    rgb, T, steps = api.render_fwd(scene, to, td, gpu_params(base))
+    cells, _, n_cells = api.trace_cells(scene, to, td, gpu_params(base), max_cells=400)
+    assert scene.get_error()[0] == 0
+    tq = torch.as_tensor(sc.tex).half().float().numpy()
+    osq = O.OracleScene(sc.sites, sc.sigma, tq, sc.offsets, sc.indices)
+    orgb, _, osteps, flags = O.render(osq, o, d, params=oracle_params(base))
+    oc, _, on, _ = O.trace(osq, o, d, max_cells=400, params=oracle_params(base))
+    compare_sequences(cells.cpu().numpy(), n_cells.cpu().numpy(), oc, on, flags)
+    ok = (flags & O.BAND_FLAGS) == 0
+    assert np.abs(rgb.cpu().numpy()[ok] - orgb[ok]).max() <= IMG_TOL
+    assert np.array_equal(steps.cpu().numpy()[ok], osteps[ok])
+    g = (np.random.default_rng(80).normal(size=(len(o), 3)) * ok[:, None]).astype(np.float32)
+    gs, gsig, gt = api.render_bwd(scene, to, td, gpu_params(base), rgb, torch.as_tensor(g, device=DEV))
+    ogs, ogsig, ogt = O.render_bwd(osq, o, d, g.astype(np.float64), params=oracle_params(base))
+    grad_close(gsig.cpu().numpy(), ogsig, "sigma")
+    grad_close(gt.cpu().numpy(), ogt, "tex")
+    grad_close(gs.cpu().numpy(), ogs, "sites")
