@@ -2,10 +2,11 @@
 // translation units of libvt.so (never installed, never seen by callers).
 //
 // Device layout of a scene (all arrays in Morton order of the sites):
-//   site [N]    float4 {x, y, z, sigma}
-//   meta [N]    int4   {csr begin, csr end, sigma bits, user id}
-//   nbr  [E]    float4 {x_j, y_j, z_j, int bits of j}   neighbour records
-//               inlined beside the CSR so the exit test needs no second load
+//   cell [N]    32-byte record {x, y, z, sigma, csr begin, csr end, user id, 0}:
+//               one sector holds everything a walk step needs about a cell
+//   nbr  [E]    float4 {n_x, n_y, n_z, int bits of j}: the offset
+//               n = s_j - s_i (each component rounded to FP32) to neighbour j,
+//               stored beside the CSR entry so the exit test needs no second load
 //   tex  [N*R*R] RGBA texel: float4 (FP32) or 4 x 16-bit (FP16 / BF16)
 //   perm [N]    Morton index -> user id,  inv [N] user id -> Morton index
 #pragma once
@@ -22,13 +23,17 @@
 #define VT_EBIT_CAPACITY 2u
 #define VT_EBIT_BAD_RAY 4u
 
+struct __align__(32) vt_cell {
+  float x, y, z, sigma;
+  int beg, end, uid, pad;
+};
+
 struct vt_scene {
   int64_t n = 0;
   int64_t E = 0;
   int32_t R = 0;
   int32_t dtype = VT_F32;
-  float4* site = nullptr;
-  int4* meta = nullptr;
+  vt_cell* cell = nullptr;
   float4* nbr = nullptr;
   void* tex = nullptr;
   int32_t* perm = nullptr;

@@ -28,19 +28,23 @@ namespace {
 
 enum Mode { FWD = 0, BWD = 1, TRACE = 2 };
 
-// minimum resident 256-thread blocks per SM requested for the walk kernel
-#ifndef VT_WALK_MINB
-#define VT_WALK_MINB 2
+// minimum resident 256-thread blocks per SM requested for the walk kernels
+// (forward: more warps hide the walk's dependent loads; backward: more
+// registers for the adjoint state)
+#ifndef VT_FWD_MINB
+#define VT_FWD_MINB 3
+#endif
+#ifndef VT_BWD_MINB
+#define VT_BWD_MINB 2
 #endif
 // 1: issue a cell's texel loads before its exit search (latency overlapped,
 // more live registers); 0: after it
 #ifndef VT_TEX_EARLY
-#define VT_TEX_EARLY 1
+#define VT_TEX_EARLY 0
 #endif
 
 struct Scene {
-  const float4* __restrict__ site;
-  const int4* __restrict__ meta;
+  const vt_cell* __restrict__ cell;
   const float4* __restrict__ nbr;
   const void* __restrict__ tex;
   int64_t n;
@@ -208,11 +212,23 @@ __device__ __forceinline__ float exact_nd(float3 si, float3 sj, float3 d) {
   return __fadd_rn(s2, __fadd_rn(__fadd_rn(c1, c2), e));
 }
 
-// FP64 re-evaluation of a grazing plane from the FP32 inputs: returns false if
-// the plane is not crossed forward, else the exact-in-FP64 step dt (as num/1).
-__device__ __noinline__ bool grazing_fp64(float4 q, float3 si, float3 o, float3 d, float th, float tl, float* dt) {
+// A cell record is two 16-byte halves: {x, y, z, sigma} and {begin, end, uid, 0}.
+__device__ __forceinline__ float4 cell_pos(const vt_cell* c, int i) {
+  return __ldg(reinterpret_cast<const float4*>(c + i));
+}
+__device__ __forceinline__ int4 cell_csr(const vt_cell* c, int i) {
+  return __ldg(reinterpret_cast<const int4*>(c + i) + 1);
+}
+
+// FP64 re-evaluation of a grazing plane from the FP32 inputs (exact site
+// positions, not the rounded offset): returns false if the plane is not
+// crossed forward, else the step dt to it.
+__device__ __noinline__ bool grazing_fp64(const vt_cell* cells, int j, float3 si, float3 o, float3 d, float th,
+                                          float tl, float* dt) {
+  const float4 sj = cell_pos(cells, j);
   const double t64 = (double)th + (double)tl;
-  const double n0 = (double)q.x - (double)si.x, n1 = (double)q.y - (double)si.y, n2 = (double)q.z - (double)si.z;
+  const double n0 = (double)sj.x - (double)si.x, n1 = (double)sj.y - (double)si.y,
+               n2 = (double)sj.z - (double)si.z;
   const double den64 = n0 * (double)d.x + n1 * (double)d.y + n2 * (double)d.z;
   if (!(den64 > 0.0)) return false;
   const double r0 = (double)si.x - ((double)o.x + t64 * (double)d.x),
@@ -228,18 +244,18 @@ __device__ __noinline__ bool grazing_fp64(float4 q, float3 si, float3 o, float3 
 // so it ends; a local minimum over the Delaunay neighbours is the nearest
 // site (Delaunay property).
 __device__ int greedy_nearest(const Scene& S, int cell, float3 q, int max_steps, bool& ok) {
-  float4 s0 = __ldg(S.site + cell);
+  const float4 s0 = cell_pos(S.cell, cell);
   float best = dist2(q, s0.x, s0.y, s0.z);
-  int best_uid = __ldg(&S.meta[cell].w);
+  int best_uid = cell_csr(S.cell, cell).z;
   for (int it = 0; it < max_steps; ++it) {
-    int4 m = __ldg(S.meta + cell);
+    const int4 m = cell_csr(S.cell, cell);
     int bc = cell;
     for (int p = m.x; p < m.y; ++p) {
-      float4 r = __ldg(S.nbr + p);
-      float dd = dist2(q, r.x, r.y, r.z);
+      const int j = __float_as_int(__ldg(&S.nbr[p].w));
+      const float4 sj = cell_pos(S.cell, j);
+      const float dd = dist2(q, sj.x, sj.y, sj.z);
       if (dd <= best) {
-        int j = __float_as_int(r.w);
-        int uid = __ldg(&S.meta[j].w);
+        const int uid = cell_csr(S.cell, j).z;
         if (dd < best || uid < best_uid) {
           best = dd;
           best_uid = uid;
@@ -262,9 +278,9 @@ __global__ void k_anchor_nn(Scene S, const float* __restrict__ o, int64_t stride
   float3 q = make_float3(o[3 * a * stride], o[3 * a * stride + 1], o[3 * a * stride + 2]);
   unsigned long long best = ~0ull;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.n; i += (int64_t)gridDim.x * blockDim.x) {
-    float4 s = __ldg(S.site + i);
-    float dd = dist2(q, s.x, s.y, s.z);
-    unsigned long long k = ((unsigned long long)__float_as_uint(dd) << 32) | (unsigned)__ldg(&S.meta[i].w);
+    const float4 s = cell_pos(S.cell, (int)i);
+    const float dd = dist2(q, s.x, s.y, s.z);
+    unsigned long long k = ((unsigned long long)__float_as_uint(dd) << 32) | (unsigned)cell_csr(S.cell, (int)i).z;
     best = k < best ? k : best;
   }
   for (int off = 16; off > 0; off >>= 1) {
@@ -302,18 +318,33 @@ __device__ __forceinline__ int64_t ray_of_thread(const RP& P, int64_t tid) {
 }
 
 // ---------------------------------------------------------------- the walk
+// (hi, lo) -= w * c exactly up to the float-float rounding (TwoProd + TwoSum)
+__device__ __forceinline__ void ff_fma_acc(float& hi, float& lo, float w, float c, float sign) {
+  const float p = __fmul_rn(w, c);
+  const float pe = __fmaf_rn(w, c, -p);
+  float s, e;
+  two_sum(hi, sign * p, s, e);
+  lo = __fadd_rn(lo, __fmaf_rn(sign, pe, e));
+  hi = s;
+}
+
+template <int MODE>
+struct WalkBounds {
+  static constexpr int minb = MODE == FWD ? VT_FWD_MINB : (MODE == BWD ? VT_BWD_MINB : 2);
+};
+
 template <int MODE, int DT>
-__global__ void __launch_bounds__(256, VT_WALK_MINB) k_walk(Scene S, RP P, const float* __restrict__ O,
-                                                            const float* __restrict__ D,
-                                                            const int32_t* __restrict__ anchor_cell,
-                                                            float* __restrict__ rgb_out, float* __restrict__ T_out,
-                                                            int32_t* __restrict__ steps_out, Grad G, Trace TR) {
+__global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
+    k_walk(Scene S, RP P, const float* __restrict__ O, const float* __restrict__ D,
+           const int32_t* __restrict__ anchor_cell, float* __restrict__ rgb_out, float* __restrict__ T_out,
+           int32_t* __restrict__ steps_out, Grad G, Trace TR) {
   const int64_t ray = ray_of_thread(P, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
   if (ray < 0) return;
   const float3 o = make_float3(O[3 * ray], O[3 * ray + 1], O[3 * ray + 2]);
   const float3 d = make_float3(D[3 * ray], D[3 * ray + 1], D[3 * ray + 2]);
   const float dd = __fmaf_rn(d.x, d.x, __fmaf_rn(d.y, d.y, __fmul_rn(d.z, d.z)));
-  float C0 = 0.f, C1 = 0.f, C2 = 0.f;
+  // colour (FWD) as float-float: C = Ch + Cl
+  float Ch0 = 0.f, Ch1 = 0.f, Ch2 = 0.f, Cl0 = 0.f, Cl1 = 0.f, Cl2 = 0.f;
   float T = 1.f;
   int k = 0;
   const bool bad = !(dd > 0.f) || !isfinite(dd) || !isfinite(o.x) || !isfinite(o.y) || !isfinite(o.z);
@@ -338,39 +369,45 @@ __global__ void __launch_bounds__(256, VT_WALK_MINB) k_walk(Scene S, RP P, const
   } else if (t1 > t0) {
     const Taps tp = taps_for(d, S.R);
     const float G2dd = __fmul_rn(1e-12f, dd);  // grazing: (n.d)^2 <= 1e-12 |n|^2 |d|^2
-    // BWD: g = dL/dC, S = C_out - (prefix of w c) = suffix S_k after step k
-    float g0 = 0.f, g1 = 0.f, g2 = 0.f, S0 = 0.f, S1 = 0.f, S2 = 0.f;
+    // BWD: g = dL/dC and the suffix S_k = C_out - sum_{m<=k} w_m c_m as float-float
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f, Sh0 = 0.f, Sh1 = 0.f, Sh2 = 0.f, Sl0 = 0.f, Sl1 = 0.f, Sl2 = 0.f;
     if (MODE == BWD) {
       g0 = G.grad[3 * ray];
       g1 = G.grad[3 * ray + 1];
       g2 = G.grad[3 * ray + 2];
-      S0 = G.rgb[3 * ray];
-      S1 = G.rgb[3 * ray + 1];
-      S2 = G.rgb[3 * ray + 2];
+      Sh0 = G.rgb[3 * ray];
+      Sh1 = G.rgb[3 * ray + 1];
+      Sh2 = G.rgb[3 * ray + 2];
     }
-    // start cell: greedy walk from this ray's anchor cell to the origin
-    bool ok = true;
-    int cell = greedy_nearest(S, anchor_cell[ray / P.anchor_stride], o, P.max_steps, ok);
-    if (!ok) atomicOr(S.err, (unsigned long long)VT_EBIT_MAX_STEPS);
-    float3 si;
+    // start cell: the anchor's cell if the origin is the anchor point, else a
+    // greedy walk from it to the origin
+    int cell;
     {
-      const float4 s4 = __ldg(S.site + cell);
-      si = make_float3(s4.x, s4.y, s4.z);
+      const int64_t a = ray / P.anchor_stride;
+      const int64_t ar = a * P.anchor_stride;
+      cell = anchor_cell[a];
+      if (O[3 * ar] != o.x || O[3 * ar + 1] != o.y || O[3 * ar + 2] != o.z) {
+        bool ok = true;
+        cell = greedy_nearest(S, cell, o, P.max_steps, ok);
+        if (!ok) atomicOr(S.err, (unsigned long long)VT_EBIT_MAX_STEPS);
+      }
     }
     float th = 0.f, tl = 0.f;  // entry parameter of the current cell (float-float)
-    // BWD carry: previous cell, its sigma * dL/dtau, site gradient so far,
-    // dL/dsigma, its site position; whether the entry crossing is differentiable
+    // BWD carry: previous cell, its sigma * dL/dtau, its dL/dsigma, site
+    // gradient so far and position; whether the entry crossing is differentiable
     int pc = -1;
     float p_sdtau = 0.f, p_gsig = 0.f;
-    float3 p_gs = make_float3(0.f, 0.f, 0.f), p_s = si;
+    float3 p_gs = make_float3(0.f, 0.f, 0.f), p_s = make_float3(0.f, 0.f, 0.f);
     bool cross_valid = false;
     for (;;) {
       if (k >= P.max_steps) {
         atomicOr(S.err, (unsigned long long)VT_EBIT_MAX_STEPS);
         break;
       }
-      const int4 m = __ldg(S.meta + cell);
-      const float sig = __int_as_float(m.z);
+      const float4 cp = cell_pos(S.cell, cell);
+      const int4 m = cell_csr(S.cell, cell);
+      const float3 si = make_float3(cp.x, cp.y, cp.z);
+      const float sig = cp.w;
       // texels of this cell (independent of the exit search)
       TexRaw<DT> tx0, tx1, tx2, tx3;
       const int64_t tb0 = (int64_t)cell * S.RR + tp.base;
@@ -381,21 +418,19 @@ __global__ void __launch_bounds__(256, VT_WALK_MINB) k_walk(Scene S, RP P, const
         tx3 = load_texel<DT>(S.tex, tb0 + tp.sx + tp.sy);
       }
       const float3 r = rel_pos(si, o, d, th, tl);
-      // ---- exit search over the Delaunay neighbours
+      // ---- exit search over the Delaunay neighbours (offset records n = s_j - s_i)
       float bn = 1.f, bd = 0.f;  // best dt = bn / bd (bd == 0: none yet)
       int bj = -1;
-      float3 bq = si;
 #pragma unroll 2
       for (int p = m.x; p < m.y; ++p) {
         const float4 q = __ldg(S.nbr + p);
-        const float nx = __fsub_rn(q.x, si.x), ny = __fsub_rn(q.y, si.y), nz = __fsub_rn(q.z, si.z);
-        float den = __fmaf_rn(nx, d.x, __fmaf_rn(ny, d.y, __fmul_rn(nz, d.z)));
-        const float nn = __fmaf_rn(nx, nx, __fmaf_rn(ny, ny, __fmul_rn(nz, nz)));
-        float num = __fmaf_rn(nx, r.x, __fmaf_rn(ny, r.y, __fmaf_rn(nz, r.z, __fmul_rn(0.5f, nn))));
+        float den = __fmaf_rn(q.x, d.x, __fmaf_rn(q.y, d.y, __fmul_rn(q.z, d.z)));
+        const float nn = __fmaf_rn(q.x, q.x, __fmaf_rn(q.y, q.y, __fmul_rn(q.z, q.z)));
+        float num = __fmaf_rn(q.x, r.x, __fmaf_rn(q.y, r.y, __fmaf_rn(q.z, r.z, __fmul_rn(0.5f, nn))));
         if (__fmul_rn(den, den) <= __fmul_rn(G2dd, nn)) {
           // grazing plane: FP64 recheck from the FP32 inputs
           atomicAdd(S.err + 1, 1ull);
-          if (!grazing_fp64(q, si, o, d, th, tl, &num)) continue;
+          if (!grazing_fp64(S.cell, __float_as_int(q.w), si, o, d, th, tl, &num)) continue;
           den = 1.f;
         } else if (!(den > 0.f)) {
           continue;
@@ -404,7 +439,6 @@ __global__ void __launch_bounds__(256, VT_WALK_MINB) k_walk(Scene S, RP P, const
           bn = num;
           bd = den;
           bj = __float_as_int(q.w);
-          bq = make_float3(q.x, q.y, q.z);
         }
       }
       ++k;
@@ -424,7 +458,7 @@ __global__ void __launch_bounds__(256, VT_WALK_MINB) k_walk(Scene S, RP P, const
       if (MODE == TRACE) {
         const int64_t slot = ray * (int64_t)TR.max_cells + (k - 1);
         if (k <= TR.max_cells) {
-          TR.cells[slot] = m.w;
+          TR.cells[slot] = m.z;
           if (TR.t_exit) TR.t_exit[slot] = bj >= 0 ? __fadd_rn(eh, el) : INFINITY;
         }
       }
@@ -457,18 +491,18 @@ __global__ void __launch_bounds__(256, VT_WALK_MINB) k_walk(Scene S, RP P, const
           c1 = __fmaf_rn(tw[3], a3.y, __fmaf_rn(tw[2], a2.y, __fmaf_rn(tw[1], a1.y, __fmul_rn(tw[0], a0.y))));
           c2 = __fmaf_rn(tw[3], a3.z, __fmaf_rn(tw[2], a2.z, __fmaf_rn(tw[1], a1.z, __fmul_rn(tw[0], a0.z))));
           if (MODE == FWD) {
-            C0 = __fmaf_rn(w, c0, C0);
-            C1 = __fmaf_rn(w, c1, C1);
-            C2 = __fmaf_rn(w, c2, C2);
-          } else {
-            S0 = __fsub_rn(S0, __fmul_rn(w, c0));
-            S1 = __fsub_rn(S1, __fmul_rn(w, c1));
-            S2 = __fsub_rn(S2, __fmul_rn(w, c2));
+            ff_fma_acc(Ch0, Cl0, w, c0, 1.f);
+            ff_fma_acc(Ch1, Cl1, w, c1, 1.f);
+            ff_fma_acc(Ch2, Cl2, w, c2, 1.f);
+          } else if (MODE == BWD) {
+            ff_fma_acc(Sh0, Sl0, w, c0, -1.f);
+            ff_fma_acc(Sh1, Sl1, w, c1, -1.f);
+            ff_fma_acc(Sh2, Sl2, w, c2, -1.f);
           }
         }
         if (MODE == BWD) {
           // dL/dtau_k = g . (T_{k+1} c_k - S_k)
-          dtau = g0 * (Tn * c0 - S0) + g1 * (Tn * c1 - S1) + g2 * (Tn * c2 - S2);
+          dtau = g0 * ((Tn * c0 - Sh0) - Sl0) + g1 * ((Tn * c1 - Sh1) - Sl1) + g2 * ((Tn * c2 - Sh2) - Sl2);
         }
         T = Tn;
         if (T < P.T_eps) stop = true;
@@ -489,12 +523,11 @@ __global__ void __launch_bounds__(256, VT_WALK_MINB) k_walk(Scene S, RP P, const
         if (pc >= 0 && (p_gs.x != 0.f || p_gs.y != 0.f || p_gs.z != 0.f || p_gsig != 0.f))
           atomicAdd(G.g_cell + pc, make_float4(p_gs.x, p_gs.y, p_gs.z, p_gsig));
         if (coloured && w > 0.f) {
-          const int64_t b0 = tb0;
           const float ww0 = w * tw[0], ww1 = w * tw[1], ww2 = w * tw[2], ww3 = w * tw[3];
-          if (ww0 != 0.f) atomicAdd(G.g_tex + b0, make_float4(g0 * ww0, g1 * ww0, g2 * ww0, 0.f));
-          if (ww1 != 0.f) atomicAdd(G.g_tex + b0 + tp.sx, make_float4(g0 * ww1, g1 * ww1, g2 * ww1, 0.f));
-          if (ww2 != 0.f) atomicAdd(G.g_tex + b0 + tp.sy, make_float4(g0 * ww2, g1 * ww2, g2 * ww2, 0.f));
-          if (ww3 != 0.f) atomicAdd(G.g_tex + b0 + tp.sx + tp.sy, make_float4(g0 * ww3, g1 * ww3, g2 * ww3, 0.f));
+          if (ww0 != 0.f) atomicAdd(G.g_tex + tb0, make_float4(g0 * ww0, g1 * ww0, g2 * ww0, 0.f));
+          if (ww1 != 0.f) atomicAdd(G.g_tex + tb0 + tp.sx, make_float4(g0 * ww1, g1 * ww1, g2 * ww1, 0.f));
+          if (ww2 != 0.f) atomicAdd(G.g_tex + tb0 + tp.sy, make_float4(g0 * ww2, g1 * ww2, g2 * ww2, 0.f));
+          if (ww3 != 0.f) atomicAdd(G.g_tex + tb0 + tp.sx + tp.sy, make_float4(g0 * ww3, g1 * ww3, g2 * ww3, 0.f));
         }
         pc = cell;
         p_sdtau = sig * dtau;
@@ -505,10 +538,12 @@ __global__ void __launch_bounds__(256, VT_WALK_MINB) k_walk(Scene S, RP P, const
         cross_valid = (bj >= 0) && !exit_beyond && ff_gt(eh, el, t0);
         if (stop && cross_valid) {
           // terminated inside the extent: the exit plane still moves delta_K
+          const float4 q4 = cell_pos(S.cell, bj);
+          const float3 sj = make_float3(q4.x, q4.y, q4.z);
           const float3 re = rel_pos(si, o, d, eh, el);  // s_K - x_out
-          const float nd = exact_nd(si, bq, d);
+          const float nd = exact_nd(si, sj, d);
           const float dtb = p_sdtau / nd;
-          const float nx = __fsub_rn(bq.x, si.x), ny = __fsub_rn(bq.y, si.y), nz = __fsub_rn(bq.z, si.z);
+          const float nx = __fsub_rn(sj.x, si.x), ny = __fsub_rn(sj.y, si.y), nz = __fsub_rn(sj.z, si.z);
           p_gs.x -= dtb * re.x;
           p_gs.y -= dtb * re.y;
           p_gs.z -= dtb * re.z;
@@ -517,24 +552,25 @@ __global__ void __launch_bounds__(256, VT_WALK_MINB) k_walk(Scene S, RP P, const
       }
       if (stop || exit_beyond) break;
       cell = bj;
-      si = bq;
       th = eh;
       tl = el;
     }
     if (MODE == BWD && pc >= 0 && (p_gs.x != 0.f || p_gs.y != 0.f || p_gs.z != 0.f || p_gsig != 0.f))
       atomicAdd(G.g_cell + pc, make_float4(p_gs.x, p_gs.y, p_gs.z, p_gsig));
-    C0 = __fmaf_rn(T, P.bg.x, C0);
-    C1 = __fmaf_rn(T, P.bg.y, C1);
-    C2 = __fmaf_rn(T, P.bg.z, C2);
+    if (MODE == FWD) {
+      ff_fma_acc(Ch0, Cl0, T, P.bg.x, 1.f);
+      ff_fma_acc(Ch1, Cl1, T, P.bg.y, 1.f);
+      ff_fma_acc(Ch2, Cl2, T, P.bg.z, 1.f);
+    }
   } else {
-    C0 = P.bg.x;
-    C1 = P.bg.y;
-    C2 = P.bg.z;
+    Ch0 = P.bg.x;
+    Ch1 = P.bg.y;
+    Ch2 = P.bg.z;
   }
   if (MODE == FWD) {
-    rgb_out[3 * ray] = C0;
-    rgb_out[3 * ray + 1] = C1;
-    rgb_out[3 * ray + 2] = C2;
+    rgb_out[3 * ray] = __fadd_rn(Ch0, Cl0);
+    rgb_out[3 * ray + 1] = __fadd_rn(Ch1, Cl1);
+    rgb_out[3 * ray + 2] = __fadd_rn(Ch2, Cl2);
     if (T_out) T_out[ray] = T;
     if (steps_out) steps_out[ray] = k;
   } else if (MODE == TRACE) {
@@ -544,12 +580,12 @@ __global__ void __launch_bounds__(256, VT_WALK_MINB) k_walk(Scene S, RP P, const
 }
 
 // user-order gradients from the Morton-ordered scratch (overwrites outputs)
-__global__ void k_grad_out(int64_t n, int RR, const int4* __restrict__ meta, const float4* __restrict__ g_cell,
+__global__ void k_grad_out(int64_t n, int RR, const vt_cell* __restrict__ cells, const float4* __restrict__ g_cell,
                            const float4* __restrict__ g_tex, float* gs, float* gsig, float* gtex) {
   int64_t total = n * RR;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = e / RR, t = e - i * RR;
-    int64_t u = __ldg(&meta[i].w);
+    int64_t u = cell_csr(cells, (int)i).z;
     if (gtex) {
       float4 g = g_tex[e];
       float* dst = gtex + (u * RR + t) * 3;
@@ -612,8 +648,7 @@ int64_t walk_threads(const RP& P) {
 
 Scene scene_view(vt_scene* s) {
   Scene S;
-  S.site = s->site;
-  S.meta = s->meta;
+  S.cell = s->cell;
   S.nbr = s->nbr;
   S.tex = s->tex;
   S.n = s->n;
@@ -693,7 +728,7 @@ vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float
     if (r != VT_OK) return r;
   }
   if (grad_sites || grad_sigma || grad_tex) {
-    k_grad_out<<<vt_grid(s->n * RR, 256, 152 * 64), 256, 0, st>>>(s->n, (int)RR, s->meta, s->g_cell, s->g_tex,
+    k_grad_out<<<vt_grid(s->n * RR, 256, 152 * 64), 256, 0, st>>>(s->n, (int)RR, s->cell, s->g_cell, s->g_tex,
                                                                     grad_sites, grad_sigma, grad_tex);
     VT_CUDA_TRY(cudaGetLastError());
   }

@@ -137,39 +137,40 @@ __global__ void k_degree(int64_t n, const int32_t* __restrict__ perm, const int6
   }
 }
 
-// site/meta (positions, sigma) in Morton order
+// cell records (position, sigma, CSR range, user id) in Morton order
 __global__ void k_fill_cells(int64_t n, const int32_t* __restrict__ perm, const float* __restrict__ sites,
                              const float* __restrict__ sigma, const int32_t* __restrict__ beg,
-                             const int32_t* __restrict__ deg, float4* __restrict__ site, int4* __restrict__ meta,
-                             int keep_csr) {
+                             const int32_t* __restrict__ deg, vt_cell* __restrict__ cell, int keep_csr) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int32_t u = perm[i];
-    float4 s = site[i];
-    if (sites) s = make_float4(sites[3 * (int64_t)u], sites[3 * (int64_t)u + 1], sites[3 * (int64_t)u + 2], s.w);
-    if (sigma) s.w = sigma[u];
-    site[i] = s;
-    int4 m = meta[i];
-    if (!keep_csr) {
-      m.x = beg[i];
-      m.y = beg[i] + deg[i];
-      m.w = u;
+    vt_cell c = cell[i];
+    if (sites) {
+      c.x = sites[3 * (int64_t)u];
+      c.y = sites[3 * (int64_t)u + 1];
+      c.z = sites[3 * (int64_t)u + 2];
     }
-    m.z = __float_as_int(s.w);
-    meta[i] = m;
+    if (sigma) c.sigma = sigma[u];
+    if (!keep_csr) {
+      c.beg = beg[i];
+      c.end = beg[i] + deg[i];
+      c.uid = u;
+      c.pad = 0;
+    }
+    cell[i] = c;
   }
 }
 
-// neighbour records {x_j, y_j, z_j, j} in the user's CSR order of each row
-__global__ void k_fill_nbr(int64_t n, const int4* __restrict__ meta, const int64_t* __restrict__ off,
+// neighbour records {s_j - s_i, j} in the user's CSR order of each row
+__global__ void k_fill_nbr(int64_t n, const vt_cell* __restrict__ cell, const int64_t* __restrict__ off,
                            const int32_t* __restrict__ idx, const int32_t* __restrict__ inv,
-                           const float4* __restrict__ site, float4* __restrict__ nbr) {
+                           float4* __restrict__ nbr) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    int4 m = meta[i];
-    int64_t ub = off[m.w];
-    for (int p = m.x; p < m.y; ++p) {
-      int32_t j = inv[idx[ub + (p - m.x)]];
-      float4 s = site[j];
-      nbr[p] = make_float4(s.x, s.y, s.z, __int_as_float(j));
+    const vt_cell c = cell[i];
+    int64_t ub = off[c.uid];
+    for (int p = c.beg; p < c.end; ++p) {
+      int32_t j = inv[idx[ub + (p - c.beg)]];
+      const vt_cell cj = cell[j];
+      nbr[p] = make_float4(__fsub_rn(cj.x, c.x), __fsub_rn(cj.y, c.y), __fsub_rn(cj.z, c.z), __int_as_float(j));
     }
   }
 }
@@ -240,8 +241,7 @@ vt_status validate(int64_t n, const float* sites, const float* sigma, const int6
 
 void free_scene(vt_scene* s) {
   if (!s) return;
-  cudaFree(s->site);
-  cudaFree(s->meta);
+  cudaFree(s->cell);
   cudaFree(s->nbr);
   cudaFree(s->tex);
   cudaFree(s->perm);
@@ -269,8 +269,7 @@ vt_status create_impl(const vt_scene_desc* dsc, cudaStream_t st, vt_scene* s) {
   s->R = dsc->tex_res;
   s->dtype = dsc->tex_dtype;
   const int64_t RR = (int64_t)s->R * s->R;
-  VT_CUDA_TRY(dmalloc(&s->site, n));
-  VT_CUDA_TRY(dmalloc(&s->meta, n));
+  VT_CUDA_TRY(dmalloc(&s->cell, n));
   VT_CUDA_TRY(dmalloc(&s->nbr, E > 0 ? E : 1));
   VT_CUDA_TRY(cudaMalloc(&s->tex, n * RR * vt_texel_bytes(s->dtype) + 16));
   VT_CUDA_TRY(dmalloc(&s->perm, n));
@@ -279,8 +278,7 @@ vt_status create_impl(const vt_scene_desc* dsc, cudaStream_t st, vt_scene* s) {
   VT_CUDA_TRY(dmalloc(&s->anchor_key, VT_MAX_ANCHORS));
   VT_CUDA_TRY(dmalloc(&s->anchor_cell, VT_MAX_ANCHORS));
   VT_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, 4 * sizeof(unsigned long long), st));
-  VT_CUDA_TRY(cudaMemsetAsync(s->site, 0, n * sizeof(float4), st));
-  VT_CUDA_TRY(cudaMemsetAsync(s->meta, 0, n * sizeof(int4), st));
+  VT_CUDA_TRY(cudaMemsetAsync(s->cell, 0, n * sizeof(vt_cell), st));
 
   // bounding box
   const int nb = 256;
@@ -336,8 +334,8 @@ vt_status create_impl(const vt_scene_desc* dsc, cudaStream_t st, vt_scene* s) {
       rs = VT_ERR_CUDA;
       break;
     }
-    k_fill_cells<<<g, 256, 0, st>>>(n, s->perm, dsc->sites, dsc->sigma, beg, deg, s->site, s->meta, 0);
-    k_fill_nbr<<<g, 256, 0, st>>>(n, s->meta, dsc->adj_offsets, dsc->adj_indices, s->inv, s->site, s->nbr);
+    k_fill_cells<<<g, 256, 0, st>>>(n, s->perm, dsc->sites, dsc->sigma, beg, deg, s->cell, 0);
+    k_fill_nbr<<<g, 256, 0, st>>>(n, s->cell, dsc->adj_offsets, dsc->adj_indices, s->inv, s->nbr);
     rs = pack_tex(s, dsc->tex, st);
     if (rs != VT_OK) break;
     if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) rs = VT_ERR_CUDA;
@@ -351,14 +349,13 @@ vt_status create_impl(const vt_scene_desc* dsc, cudaStream_t st, vt_scene* s) {
   return rs;
 }
 
-__global__ void k_refresh_nbr(int64_t n, const int4* __restrict__ meta, const float4* __restrict__ site,
-                              float4* __restrict__ nbr) {
+__global__ void k_refresh_nbr(int64_t n, const vt_cell* __restrict__ cell, float4* __restrict__ nbr) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    int4 m = meta[i];
-    for (int p = m.x; p < m.y; ++p) {
+    const vt_cell c = cell[i];
+    for (int p = c.beg; p < c.end; ++p) {
       float4 q = nbr[p];
-      float4 s = site[__float_as_int(q.w)];
-      nbr[p] = make_float4(s.x, s.y, s.z, q.w);
+      const vt_cell cj = cell[__float_as_int(q.w)];
+      nbr[p] = make_float4(__fsub_rn(cj.x, c.x), __fsub_rn(cj.y, c.y), __fsub_rn(cj.z, c.z), q.w);
     }
   }
 }
@@ -411,8 +408,8 @@ vt_status vt_scene_update(vt_scene* s, const float* sites, const float* sigma, c
     vt_status v = validate(s->n, sites, sigma, nullptr, nullptr, 0, st);
     if (v != VT_OK) return v;
     int g = vt_grid(s->n, 256, 152 * 32);
-    k_fill_cells<<<g, 256, 0, st>>>(s->n, s->perm, sites, sigma, nullptr, nullptr, s->site, s->meta, 1);
-    if (sites) k_refresh_nbr<<<g, 256, 0, st>>>(s->n, s->meta, s->site, s->nbr);
+    k_fill_cells<<<g, 256, 0, st>>>(s->n, s->perm, sites, sigma, nullptr, nullptr, s->cell, 1);
+    if (sites) k_refresh_nbr<<<g, 256, 0, st>>>(s->n, s->cell, s->nbr);
     VT_CUDA_TRY(cudaGetLastError());
   }
   if (tex) {

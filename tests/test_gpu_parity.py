@@ -59,8 +59,13 @@ def grad_close(g, ref, name):
     tol = GRAD_REL * np.maximum(np.abs(ref), floor)
     err = np.abs(g - ref)
     bad = err > tol
-    assert not bad.any(), (f"{name}: {bad.sum()} / {bad.size} entries off; worst rel "
-                           f"{(err / np.maximum(np.abs(ref), floor)).max():.3g}")
+    if bad.any():
+        rel = err / np.maximum(np.abs(ref), floor)
+        worst = np.argsort(rel, axis=None)[::-1][:5]
+        detail = "; ".join(f"idx {np.unravel_index(i, ref.shape)} ref {ref.flat[i]:.6g} got {g.flat[i]:.6g}"
+                           for i in worst)
+        raise AssertionError(f"{name}: {bad.sum()} / {bad.size} entries off; worst rel {rel.max():.3g}; "
+                             f"max|ref| {np.abs(ref).max():.4g}; {detail}")
 
 
 # ---------------------------------------------------------------- fixtures
