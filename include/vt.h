@@ -203,6 +203,28 @@ vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float
                         const vt_render_params* p, const float* rgb_out, const float* grad_rgb,
                         float* grad_sites, float* grad_sigma, float* grad_tex, void* stream);
 
+/* Allocation-free backward (no counterpart in the paper). Same arguments,
+ * outputs and numerics as vt_render_bwd, for callers that may not allocate
+ * device memory at the time of the call: vt_render_bwd allocates its gradient
+ * scratch with cudaMalloc on its first call for a scene, and cudaMalloc can
+ * synchronise the device and bypasses an application's own memory pool or
+ * budget (for example a framework's caching allocator). This entry point
+ * calls no cudaMalloc, cudaFree or other allocating routine; its scratch is a
+ * fixed device array of VT_STATIC_SCRATCH_BYTES (32 MiB) compiled into
+ * libvt.so, which every GPU that loads the library holds until the process
+ * exits. The scene needs n_sites * (1 + R*R) * 16 bytes of it (for R = 8,
+ * up to 32,263 sites); a larger scene returns VT_ERR_CAPACITY and does nothing.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture. All calls share the one array and clear the part they
+ * use at the start: calls whose work overlaps on the GPU (other streams, other
+ * threads, or vt_render_bwd_static on two scenes concurrently) race and give
+ * wrong gradients -- order them on one stream. */
+#define VT_STATIC_SCRATCH_BYTES (32ll * 1024 * 1024)
+vt_status vt_render_bwd_static(vt_scene* s, int64_t n_rays, const float* o, const float* d, const float* time,
+                               const vt_render_params* p, const float* rgb_out, const float* grad_rgb,
+                               float* grad_sites, float* grad_sigma, float* grad_tex, void* stream);
+
 /* Debug / parity: visited cells of each ray (walk order, USER ids) and the
  * exit parameter of each visited cell (+inf if unbounded), up to max_cells
  * per ray: cells [n_rays,max_cells] int32, t_exit [n_rays,max_cells] (NULL

@@ -21,7 +21,7 @@ VT_CAM_PINHOLE, VT_CAM_FISHEYE_EQUIDIST, VT_CAM_ROLLING_SHUTTER, VT_CAM_THIN_LEN
 # every symbol include/vt.h declares
 EXPORTS = ["vt_render_params_default", "vt_scene_create", "vt_scene_update", "vt_scene_destroy", "vt_scene_info",
            "vt_scene_get_error", "vt_camera_n_rays", "vt_generate_rays", "vt_render_fwd", "vt_render_bwd",
-           "vt_trace_cells", "vt_l2_loss", "vt_average_samples", "vt_average_samples_bwd", "vt_status_str"]
+           "vt_render_bwd_static", "vt_trace_cells", "vt_l2_loss", "vt_average_samples", "vt_average_samples_bwd", "vt_status_str"]
 
 
 class VTError(RuntimeError):
@@ -67,6 +67,7 @@ def _load():
         "vt_generate_rays": ([P, I32, P, P, P, P], C.c_int),
         "vt_render_fwd": ([P, I64, P, P, P, P, P, P, P, P], C.c_int),
         "vt_render_bwd": ([P, I64, P, P, P, P, P, P, P, P, P, P], C.c_int),
+        "vt_render_bwd_static": ([P, I64, P, P, P, P, P, P, P, P, P, P], C.c_int),
         "vt_trace_cells": ([P, I64, P, P, P, I32, P, P, P, P], C.c_int),
         "vt_l2_loss": ([I64, P, P, P, P, P], C.c_int),
         "vt_average_samples": ([I64, I32, P, P, P], C.c_int),
@@ -150,6 +151,16 @@ def vt_render_bwd(scene: int, n_rays: int, o: int, d: int, time: int, params: vt
     check(lib.vt_render_bwd(C.c_void_p(scene), n_rays, C.c_void_p(o), C.c_void_p(d), C.c_void_p(time),
                             C.byref(params), C.c_void_p(rgb), C.c_void_p(grad_rgb), C.c_void_p(grad_sites),
                             C.c_void_p(grad_sigma), C.c_void_p(grad_tex), C.c_void_p(stream)), "vt_render_bwd")
+
+
+def vt_render_bwd_static(scene: int, n_rays: int, o: int, d: int, time: int, params: vt_render_params, rgb: int,
+                         grad_rgb: int, grad_sites: int, grad_sigma: int, grad_tex: int, stream: int):
+    """Allocation-free backward (fixed 32 MiB library scratch); raises VTError
+    with VT_ERR_CAPACITY for scenes that need more."""
+    check(lib.vt_render_bwd_static(C.c_void_p(scene), n_rays, C.c_void_p(o), C.c_void_p(d), C.c_void_p(time),
+                                   C.byref(params), C.c_void_p(rgb), C.c_void_p(grad_rgb), C.c_void_p(grad_sites),
+                                   C.c_void_p(grad_sigma), C.c_void_p(grad_tex), C.c_void_p(stream)),
+          "vt_render_bwd_static")
 
 
 def vt_trace_cells(scene: int, n_rays: int, o: int, d: int, params: vt_render_params, max_cells: int, cells: int,

@@ -22,6 +22,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <mutex>
+
 #include "vt_internal.cuh"
 
 namespace {
@@ -749,6 +751,78 @@ vt_status vt_trace_cells(vt_scene* s, int64_t n_rays, const float* o, const floa
   if (r != VT_OK) return r;
   Trace TR{cells, t_exit, n_cells, max_cells};
   return launch_walk<TRACE>(s, S, P, o, d, nullptr, nullptr, nullptr, Grad{}, TR, st);
+}
+
+// ---------------------------------------------------------------- allocation-free backward
+// Backward pass for callers that cannot allocate device memory at the time of
+// the call. vt_render_bwd allocates its gradient scratch with cudaMalloc on the
+// first call for a scene; this variant instead accumulates into one fixed
+// array compiled into the library (VT_STATIC_SCRATCH_BYTES, resident on every
+// GPU that loads libvt.so until the process exits). It has no counterpart in
+// the paper.
+}  // extern "C"
+
+namespace {
+constexpr int64_t kStaticScratchFloat4 = VT_STATIC_SCRATCH_BYTES / 16;
+static __device__ __align__(256) float4 g_static_scratch[kStaticScratchFloat4];
+
+// Device address of g_static_scratch per device. The host-side name is only a
+// stand-in for the symbol, so the address is looked up once per device, with
+// that device current, and cached.
+std::mutex g_static_mu;
+void* g_static_addr[256] = {nullptr};
+
+vt_status static_scratch_addr(float4** out) {
+  int dev = -1;
+  VT_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return VT_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* ptr = nullptr;
+    VT_CUDA_TRY(cudaGetSymbolAddress(&ptr, g_static_scratch));
+    if (!ptr) return VT_ERR_CUDA;
+    g_static_addr[dev] = ptr;
+  }
+  *out = reinterpret_cast<float4*>(g_static_addr[dev]);
+  return VT_OK;
+}
+}  // namespace
+
+extern "C" {
+
+vt_status vt_render_bwd_static(vt_scene* s, int64_t n_rays, const float* o, const float* d, const float* time,
+                               const vt_render_params* p, const float* rgb_out, const float* grad_rgb,
+                               float* grad_sites, float* grad_sigma, float* grad_tex, void* stream) {
+  (void)time;
+  if (!s || n_rays < 0 || (n_rays > 0 && (!o || !d || !rgb_out || !grad_rgb))) return VT_ERR_INVALID_ARG;
+  const int64_t RR = (int64_t)s->R * s->R;
+  const int64_t need = s->n * (1 + RR);  // one float4 per cell + one per texel
+  if (need > kStaticScratchFloat4) return VT_ERR_CAPACITY;
+  RP P;
+  vt_status r = make_rp(s, n_rays > 0 ? n_rays : 0, p, P);
+  if (r != VT_OK && n_rays > 0) return r;
+  float4* base = nullptr;
+  r = static_scratch_addr(&base);
+  if (r != VT_OK) return r;
+  float4* g_cell = base;
+  float4* g_tex = base + s->n;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the array keeps the previous call's sums: clear the part this call uses
+  VT_CUDA_TRY(cudaMemsetAsync(base, 0, need * sizeof(float4), st));
+  Scene S = scene_view(s);
+  if (n_rays > 0) {
+    r = anchors(s, S, P, o, st);
+    if (r != VT_OK) return r;
+    Grad G{g_cell, g_tex, rgb_out, grad_rgb};
+    r = launch_walk<BWD>(s, S, P, o, d, nullptr, nullptr, nullptr, G, Trace{}, st);
+    if (r != VT_OK) return r;
+  }
+  if (grad_sites || grad_sigma || grad_tex) {
+    k_grad_out<<<vt_grid(s->n * RR, 256, 152 * 64), 256, 0, st>>>(s->n, (int)RR, s->cell, g_cell, g_tex,
+                                                                    grad_sites, grad_sigma, grad_tex);
+    VT_CUDA_TRY(cudaGetLastError());
+  }
+  return VT_OK;
 }
 
 }  // extern "C"
