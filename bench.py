@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the FP32/BF16 comparison timings")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ablation", action="store_true",
+                    help="also time the forward pass with the inference-stack toggles (Morton order, 4x8 tiles, "
+                         "cell skip 1e-3), cumulatively as in the paper's Sec. 6.3 ablation")
     return ap.parse_args()
 
 
@@ -168,7 +171,11 @@ def run_ours(args, ws, rank, local):
     spp = c0.lens_samples if c0.kind == 3 else 1
     n_rays = sum(c.n_rays for c in cams)
     uniform = all(c.w == c0.w and c.h == c0.h and c.n_rays == c0.n_rays for c in cams)
-    params = api.make_params(**wl.params, **(dict(img_w=c0.w * spp, img_h=c0.h, n_images=n_img) if uniform else {}))
+    if uniform:
+        layout = dict(img_w=c0.w * spp, img_h=c0.h, n_images=n_img)
+    else:  # one launch over images of different sizes (lens samples widen a row)
+        layout = dict(image_sizes=[(c.w * (c.lens_samples if c.kind == 3 else 1), c.h) for c in cams])
+    params = api.make_params(**wl.params, **layout)
     Y = torch.as_tensor(W.target_image(n_rays, wl.seed), device=dev)
 
     scenes = {}
@@ -182,6 +189,7 @@ def run_ours(args, ws, rank, local):
     rgb = torch.empty(n_rays, 3, device=dev)
     T = torch.empty(n_rays, device=dev)
     steps = torch.empty(n_rays, dtype=torch.int32, device=dev)
+    res = torch.empty(n_rays, 3, device=dev)  # float-float residual of the colour, for the backward
     N, R = wl.scene.n, wl.scene.R
     gs = torch.empty(N, 3, device=dev)
     gsig = torch.empty(N, device=dev)
@@ -194,7 +202,7 @@ def run_ours(args, ws, rank, local):
         api.generate_rays(cams, out=(o, d, tm))
         if marks:
             marks[0].record(stream)
-        api.render_fwd(scene, o, d, params, time=tm, out=(rgb, T, steps))
+        api.render_fwd(scene, o, d, params, time=tm, out=(rgb, T, steps), residual=None if fwd_only else res)
         if marks:
             marks[1].record(stream)
         if fwd_only:
@@ -202,7 +210,7 @@ def run_ours(args, ws, rank, local):
         loss, grad = api.l2_loss(rgb, Y)
         if marks:
             marks[2].record(stream)
-        api.render_bwd(scene, o, d, params, rgb, grad, time=tm, out=(gs, gsig, gt))
+        api.render_bwd(scene, o, d, params, rgb, grad, time=tm, out=(gs, gsig, gt), residual=res)
         if marks:
             marks[3].record(stream)
         return loss
@@ -261,6 +269,33 @@ def run_ours(args, ws, rank, local):
         extra[t] = {"fwd_bwd_mrays_s": round(n_rays / (m_s * 1e-3) / 1e6 * ws, 2), "ms_fwd": round(m_f, 3),
                     "ms_bwd": round(m_b, 3)}
 
+    if args.ablation:
+        # cumulative: user order + row-major 1-D rays -> + Morton -> + 4x8 tiles -> + skip 1e-3
+        base_scene = api.Scene.from_workload(wl.scene, tex_dtype=args.tex, device=dev, keep_order=True)
+        p_1d = api.make_params(**wl.params)
+        p_skip = api.make_params(**{**wl.params, "skip_weight": 1e-3}, **layout)
+        rows = []
+        for name, sc_, pp in (("base", base_scene, p_1d), ("+morton", main, p_1d), ("+tiles", main, params),
+                              ("+skip1e-3", main, p_skip)):
+            for _ in range(args.warmup):
+                api.generate_rays(cams, out=(o, d, tm))
+                api.render_fwd(sc_, o, d, pp, time=tm, out=(rgb, T, steps))
+            barrier()
+            tot = 0.0
+            for _ in range(max(3, args.steps // 2)):
+                flush.zero_()
+                a, b = ev(), ev()
+                a.record(stream)
+                api.render_fwd(sc_, o, d, pp, time=tm, out=(rgb, T, steps))
+                b.record(stream)
+                barrier()
+                tot += a.elapsed_time(b)
+            ms = tot / max(3, args.steps // 2)
+            rows.append({"config": name, "ms_fwd": round(ms, 3), "mrays_s": round(n_rays / (ms * 1e-3) / 1e6, 1),
+                         "fps": round(n_img / (ms * 1e-3), 1)})
+        extra["ablation_fwd"] = rows
+        del base_scene
+
     # end to end through the public API with host buffers: H2D target image,
     # D2H rendered image + loss, inside the timed region
     Yh = torch.as_tensor(W.target_image(n_rays, wl.seed)).pin_memory()
@@ -271,9 +306,9 @@ def run_ours(args, ws, rank, local):
     def e2e_step():
         Yd.copy_(Yh, non_blocking=True)
         api.generate_rays(cams, out=(o, d, tm))
-        api.render_fwd(main, o, d, params, time=tm, out=(rgb, T, steps))
+        api.render_fwd(main, o, d, params, time=tm, out=(rgb, T, steps), residual=res)
         loss, grad = api.l2_loss(rgb, Yd)
-        api.render_bwd(main, o, d, params, rgb, grad, time=tm, out=(gs, gsig, gt))
+        api.render_bwd(main, o, d, params, rgb, grad, time=tm, out=(gs, gsig, gt), residual=res)
         rgb_h.copy_(rgb, non_blocking=True)
         loss_h.copy_(loss, non_blocking=True)
 
@@ -294,7 +329,7 @@ def run_ours(args, ws, rank, local):
     peaks, peak_kind = measured_peaks()
     E = main.n_edges
     tb = 8 if args.tex in ("f16", "bf16") else 16
-    b_fwd_step = 16 + 16 * E / N + 4 * tb  # meta + neighbour records + 4 texels
+    b_fwd_step = 32 + 16 * E / N + 4 * tb  # cell record + neighbour plane records + 4 texels
     b_bwd_step = b_fwd_step + 2 * (16 + 4 * 16)  # + RMW of one cell and four texel gradient float4s
     io_fwd, io_bwd = 24 + 20, 24 + 24
     dom = "bwd" if ms_bwd >= ms_fwd else "fwd"

@@ -74,7 +74,11 @@ typedef struct {
   const int32_t* adj_indices;  /* [E] neighbour ids; symmetric, no self loops,
                                   no duplicates within a row, E < 2^31; may be
                                   NULL when E == 0                                 */
+  int32_t flags;               /* VT_SCENE_KEEP_ORDER: store cells in user order
+                                  instead of Morton order (for ablations)         */
 } vt_scene_desc;
+
+#define VT_SCENE_KEEP_ORDER 1
 
 /* Render parameters. Rays are r(t) = o + t d for t in [t_near, t_far],
  * optionally clipped to the box [clip_lo, clip_hi]. */
@@ -92,6 +96,10 @@ typedef struct {
   int32_t n_images;        /* number of images when img_w > 0                          */
   int32_t max_steps;       /* cells a ray may visit (<= 0: min(4N, 2^20)); exceeding it
                               stops the ray and records VT_ERR_MAX_STEPS               */
+  const int32_t* image_sizes; /* optional HOST [n_images][2] = (w, h) of each image when
+                              the images differ in size (rays laid out image after image,
+                              row-major); then img_w/img_h are ignored and n_images <= 64.
+                              NULL: img_w/img_h/n_images as above                      */
 } vt_render_params;
 
 /* Fill `p` with the defaults listed above. */
@@ -100,7 +108,8 @@ void vt_render_params_default(vt_render_params* p);
 /* Build a scene (Sec. 5.6 one-time preprocessing, untimed in the paper):
  * validates the inputs (finite sites, sigma >= 0, CSR in range, symmetric,
  * no self loops, R >= 2), sorts cells by 63-bit Morton code over the sites'
- * bounding box (ties by user id), permutes sites / densities / textures,
+ * bounding box (ties by user id; skipped with VT_SCENE_KEEP_ORDER, Sec. 6.3
+ * ablates this ordering), permutes sites / densities / textures,
  * remaps the adjacency and stores each neighbour's position inline with its
  * CSR entry, pads texels RGB -> RGBA in the requested storage dtype.
  * On success *out receives a new scene; on error *out is NULL. Synchronises
@@ -179,15 +188,20 @@ vt_status vt_generate_rays(const vt_camera* cams, int32_t n_cams, float* o, floa
  *   o, d   : DEVICE [n_rays,3] ray origins and directions (|d| > 0; t is in
  *            units of |d|; the colour uses d's direction).
  *   time   : DEVICE [n_rays] or NULL; accepted and ignored (static scene).
- *   rgb_out: DEVICE [n_rays,3] C = sum_k T_k alpha_k c_k + T_final bg.
+ *   rgb_out: DEVICE [n_rays,3] C = sum_k T_k alpha_k c_k + T_final bg
+ *            (accumulated in float-float, rounded to FP32).
  *   T_out  : DEVICE [n_rays] final transmittance (NULL allowed).
  *   steps_out: DEVICE [n_rays] int32 cells visited by the walk (NULL allowed).
+ *   rgb_residual: DEVICE [n_rays,3] or NULL: the rounding residual C - rgb_out
+ *            of the float-float colour. Passing it to vt_render_bwd lets the
+ *            backward form the suffix sums C - sum_{m<=k} w_m c_m without the
+ *            FP32 rounding of C (which limits deep-ray gradients to ~1e-3). 
  * The start cell of each ray is found by an exact nearest-site search for one
  * anchor origin per image (per 4096 rays in 1-D layout) followed by a greedy
  * walk over the Delaunay graph to the ray's own origin. */
 vt_status vt_render_fwd(vt_scene* s, int64_t n_rays, const float* o, const float* d, const float* time,
                         const vt_render_params* p, float* rgb_out, float* T_out, int32_t* steps_out,
-                        void* stream);
+                        float* rgb_residual, void* stream);
 
 /* Backward render: re-traverses every ray with decisions identical to
  * vt_render_fwd (no per-ray cell lists are stored) and accumulates
@@ -195,16 +209,17 @@ vt_status vt_render_fwd(vt_scene* s, int64_t n_rays, const float* o, const float
  *   grad_sigma [N]   (dL/dtau * delta, Eq. 3),
  *   grad_tex   [N,R,R,3] (bilinear weights * T alpha * dL/dC),
  * all DEVICE FP32 in USER index order, OVERWRITTEN (the call zero-fills them).
- * rgb_out is the forward's output for the same rays and parameters;
- * grad_rgb is dL/dC [n_rays,3]. Any of the three gradient pointers may be
+ * rgb_out is the forward's output for the same rays and parameters and
+ * rgb_residual (NULL allowed) its residual output; grad_rgb is dL/dC [n_rays,3]. Any of the three gradient pointers may be
  * NULL to skip that output. Library-owned scratch (one float4 per cell and
  * per texel) is allocated on first use and kept with the scene. */
 vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float* d, const float* time,
-                        const vt_render_params* p, const float* rgb_out, const float* grad_rgb,
-                        float* grad_sites, float* grad_sigma, float* grad_tex, void* stream);
+                        const vt_render_params* p, const float* rgb_out, const float* rgb_residual,
+                        const float* grad_rgb, float* grad_sites, float* grad_sigma, float* grad_tex,
+                        void* stream);
 
 /* Allocation-free backward (no counterpart in the paper). Same arguments,
- * outputs and numerics as vt_render_bwd, for callers that may not allocate
+ * outputs and numerics as vt_render_bwd without a colour residual, for callers that may not allocate
  * device memory at the time of the call: vt_render_bwd allocates its gradient
  * scratch with cudaMalloc on its first call for a scene, and cudaMalloc can
  * synchronise the device and bypasses an application's own memory pool or

@@ -33,14 +33,17 @@ class VTError(RuntimeError):
 class vt_scene_desc(C.Structure):
     _fields_ = [("n_sites", C.c_int64), ("tex_res", C.c_int32), ("tex_dtype", C.c_int32), ("sites", C.c_void_p),
                 ("sigma", C.c_void_p), ("tex", C.c_void_p), ("adj_offsets", C.c_void_p),
-                ("adj_indices", C.c_void_p)]
+                ("adj_indices", C.c_void_p), ("flags", C.c_int32)]
+
+
+VT_SCENE_KEEP_ORDER = 1
 
 
 class vt_render_params(C.Structure):
     _fields_ = [("t_near", C.c_float), ("t_far", C.c_float), ("use_clip_box", C.c_int32),
                 ("clip_lo", C.c_float * 3), ("clip_hi", C.c_float * 3), ("T_eps", C.c_float),
                 ("skip_weight", C.c_float), ("bg", C.c_float * 3), ("img_w", C.c_int32), ("img_h", C.c_int32),
-                ("n_images", C.c_int32), ("max_steps", C.c_int32)]
+                ("n_images", C.c_int32), ("max_steps", C.c_int32), ("image_sizes", C.c_void_p)]
 
 
 class vt_camera(C.Structure):
@@ -65,8 +68,8 @@ def _load():
         "vt_scene_get_error": ([P, P, P], C.c_int),
         "vt_camera_n_rays": ([P], I64),
         "vt_generate_rays": ([P, I32, P, P, P, P], C.c_int),
-        "vt_render_fwd": ([P, I64, P, P, P, P, P, P, P, P], C.c_int),
-        "vt_render_bwd": ([P, I64, P, P, P, P, P, P, P, P, P, P], C.c_int),
+        "vt_render_fwd": ([P, I64, P, P, P, P, P, P, P, P, P], C.c_int),
+        "vt_render_bwd": ([P, I64, P, P, P, P, P, P, P, P, P, P, P], C.c_int),
         "vt_render_bwd_static": ([P, I64, P, P, P, P, P, P, P, P, P, P], C.c_int),
         "vt_trace_cells": ([P, I64, P, P, P, I32, P, P, P, P], C.c_int),
         "vt_l2_loss": ([I64, P, P, P, P, P], C.c_int),
@@ -140,17 +143,18 @@ def vt_generate_rays(cams, o: int, d: int, time: int, stream: int):
 
 
 def vt_render_fwd(scene: int, n_rays: int, o: int, d: int, time: int, params: vt_render_params, rgb: int, T: int,
-                  steps: int, stream: int):
+                  steps: int, rgb_residual: int, stream: int):
     check(lib.vt_render_fwd(C.c_void_p(scene), n_rays, C.c_void_p(o), C.c_void_p(d), C.c_void_p(time),
-                            C.byref(params), C.c_void_p(rgb), C.c_void_p(T), C.c_void_p(steps), C.c_void_p(stream)),
-          "vt_render_fwd")
+                            C.byref(params), C.c_void_p(rgb), C.c_void_p(T), C.c_void_p(steps),
+                            C.c_void_p(rgb_residual), C.c_void_p(stream)), "vt_render_fwd")
 
 
 def vt_render_bwd(scene: int, n_rays: int, o: int, d: int, time: int, params: vt_render_params, rgb: int,
-                  grad_rgb: int, grad_sites: int, grad_sigma: int, grad_tex: int, stream: int):
+                  rgb_residual: int, grad_rgb: int, grad_sites: int, grad_sigma: int, grad_tex: int, stream: int):
     check(lib.vt_render_bwd(C.c_void_p(scene), n_rays, C.c_void_p(o), C.c_void_p(d), C.c_void_p(time),
-                            C.byref(params), C.c_void_p(rgb), C.c_void_p(grad_rgb), C.c_void_p(grad_sites),
-                            C.c_void_p(grad_sigma), C.c_void_p(grad_tex), C.c_void_p(stream)), "vt_render_bwd")
+                            C.byref(params), C.c_void_p(rgb), C.c_void_p(rgb_residual), C.c_void_p(grad_rgb),
+                            C.c_void_p(grad_sites), C.c_void_p(grad_sigma), C.c_void_p(grad_tex), C.c_void_p(stream)),
+          "vt_render_bwd")
 
 
 def vt_render_bwd_static(scene: int, n_rays: int, o: int, d: int, time: int, params: vt_render_params, rgb: int,

@@ -8,6 +8,8 @@ which re-traverses each ray (recomputation in place of storing the walk).
 """
 from __future__ import annotations
 
+import ctypes
+
 import torch
 
 from . import _vt
@@ -31,7 +33,8 @@ def _dev_f32(x, device):
 class Scene:
     """A Voronoi scene resident on the GPU (library-owned, Morton-ordered)."""
 
-    def __init__(self, sites, sigma, tex, adj_offsets, adj_indices, tex_dtype="f32", device="cuda"):
+    def __init__(self, sites, sigma, tex, adj_offsets, adj_indices, tex_dtype="f32", device="cuda",
+                 keep_order=False):
         device = torch.device(device)
         self.device = device
         sites = _dev_f32(sites, device)
@@ -46,14 +49,15 @@ class Scene:
         self.n, self.R = n, tex.shape[1]
         self.tex_dtype = _DTYPES[tex_dtype] if isinstance(tex_dtype, str) else int(tex_dtype)
         desc = _vt.vt_scene_desc(n, self.R, self.tex_dtype, sites.data_ptr(), sigma.data_ptr(), tex.data_ptr(),
-                                 off.data_ptr(), idx.data_ptr())
+                                 off.data_ptr(), idx.data_ptr(), _vt.VT_SCENE_KEEP_ORDER if keep_order else 0)
         with torch.cuda.device(device):
             self.handle = _vt.vt_scene_create(desc, _stream())
         self.n_edges = _vt.vt_scene_info(self.handle)[3]
 
     @classmethod
-    def from_workload(cls, sc, tex_dtype="f32", device="cuda"):
-        return cls(sc.sites, sc.sigma, sc.tex, sc.offsets, sc.indices, tex_dtype=tex_dtype, device=device)
+    def from_workload(cls, sc, tex_dtype="f32", device="cuda", keep_order=False):
+        return cls(sc.sites, sc.sigma, sc.tex, sc.offsets, sc.indices, tex_dtype=tex_dtype, device=device,
+                   keep_order=keep_order)
 
     def update(self, sites=None, sigma=None, tex=None):
         keep = [None if x is None else _dev_f32(x, self.device) for x in (sites, sigma, tex)]
@@ -76,7 +80,10 @@ class Scene:
 
 
 def make_params(t_near=0.0, t_far=20.0, use_clip_box=False, clip_lo=(0, 0, 0), clip_hi=(1, 1, 1), T_eps=1e-4,
-                skip_weight=0.0, bg=(1, 1, 1), img_w=0, img_h=0, n_images=0, max_steps=0):
+                skip_weight=0.0, bg=(1, 1, 1), img_w=0, img_h=0, n_images=0, max_steps=0, image_sizes=None):
+    """Render parameters. image_sizes: optional list of (w, h) per image for
+    launches whose images differ in size (e.g. pinhole and 4-sample thin-lens
+    views in one launch)."""
     p = _vt.vt_render_params()
     p.t_near, p.t_far, p.use_clip_box = t_near, t_far, int(bool(use_clip_box))
     p.clip_lo[:] = list(clip_lo)
@@ -84,6 +91,11 @@ def make_params(t_near=0.0, t_far=20.0, use_clip_box=False, clip_lo=(0, 0, 0), c
     p.T_eps, p.skip_weight = T_eps, skip_weight
     p.bg[:] = list(bg)
     p.img_w, p.img_h, p.n_images, p.max_steps = img_w, img_h, n_images, max_steps
+    if image_sizes is not None:
+        arr = (ctypes.c_int32 * (2 * len(image_sizes)))(*[int(v) for wh in image_sizes for v in wh])
+        p._image_sizes_keepalive = arr  # the struct holds a raw pointer to it
+        p.image_sizes = ctypes.cast(arr, ctypes.c_void_p)
+        p.n_images = len(image_sizes)
     return p
 
 
@@ -114,7 +126,10 @@ def generate_rays(cameras, device="cuda", out=None):
     return o, d, t
 
 
-def render_fwd(scene: Scene, o, d, params, time=None, out=None, want_steps=True):
+def render_fwd(scene: Scene, o, d, params, time=None, out=None, want_steps=True, residual=None):
+    """Forward render; returns (rgb, T, steps). If `residual` is a [n,3] tensor
+    it receives C - rgb (the float-float colour's rounding residual) for an
+    exact backward."""
     n = o.shape[0]
     if out is None:
         rgb = torch.empty(n, 3, device=o.device)
@@ -123,11 +138,12 @@ def render_fwd(scene: Scene, o, d, params, time=None, out=None, want_steps=True)
     else:
         rgb, T, steps = out
     _vt.vt_render_fwd(scene.handle, n, o.data_ptr(), d.data_ptr(), _ptr(time), params, rgb.data_ptr(), _ptr(T),
-                      _ptr(steps), _stream())
+                      _ptr(steps), _ptr(residual), _stream())
     return rgb, T, steps
 
 
-def render_bwd(scene: Scene, o, d, params, rgb, grad_rgb, time=None, out=None, need=(True, True, True)):
+def render_bwd(scene: Scene, o, d, params, rgb, grad_rgb, time=None, out=None, need=(True, True, True),
+               residual=None):
     dev = o.device
     if out is None:
         gs = torch.empty(scene.n, 3, device=dev) if need[0] else None
@@ -136,7 +152,7 @@ def render_bwd(scene: Scene, o, d, params, rgb, grad_rgb, time=None, out=None, n
     else:
         gs, gsig, gt = out
     _vt.vt_render_bwd(scene.handle, o.shape[0], o.data_ptr(), d.data_ptr(), _ptr(time), params, rgb.data_ptr(),
-                      grad_rgb.contiguous().data_ptr(), _ptr(gs), _ptr(gsig), _ptr(gt), _stream())
+                      _ptr(residual), grad_rgb.contiguous().data_ptr(), _ptr(gs), _ptr(gsig), _ptr(gt), _stream())
     return gs, gsig, gt
 
 
@@ -180,16 +196,17 @@ class VTRender(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, sites, sigma, tex, o, d, scene, params):
-        rgb, _, _ = render_fwd(scene, o, d, params, want_steps=False)
+        res = torch.empty(o.shape[0], 3, device=o.device)
+        rgb, _, _ = render_fwd(scene, o, d, params, want_steps=False, residual=res)
         ctx.scene, ctx.params = scene, params
-        ctx.save_for_backward(o, d, rgb)
+        ctx.save_for_backward(o, d, rgb, res)
         return rgb
 
     @staticmethod
     def backward(ctx, grad_rgb):
-        o, d, rgb = ctx.saved_tensors
+        o, d, rgb, res = ctx.saved_tensors
         need = ctx.needs_input_grad[:3]
-        gs, gsig, gt = render_bwd(ctx.scene, o, d, ctx.params, rgb, grad_rgb, need=need)
+        gs, gsig, gt = render_bwd(ctx.scene, o, d, ctx.params, rgb, grad_rgb, need=need, residual=res)
         return gs, gsig, gt, None, None, None, None
 
 

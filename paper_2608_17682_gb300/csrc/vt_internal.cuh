@@ -2,8 +2,9 @@
 // translation units of libvt.so (never installed, never seen by callers).
 //
 // Device layout of a scene (all arrays in Morton order of the sites):
-//   cell [N]    32-byte record {x, y, z, sigma, csr begin, csr end, user id, 0}:
-//               one sector holds everything a walk step needs about a cell
+//   cell [N]    32-byte record {x, y, z, sigma, csr begin, csr end, user id,
+//               nmax}: one sector holds everything a walk step needs about a
+//               cell; nmax (float bits) = max over its neighbours of |s_j - s_i|
 //   nbr  [E]    float4 {n_x, n_y, n_z, int bits of j}: the offset
 //               n = s_j - s_i (each component rounded to FP32) to neighbour j,
 //               stored beside the CSR entry so the exit test needs no second load

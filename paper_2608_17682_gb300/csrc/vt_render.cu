@@ -13,7 +13,7 @@
 // the cell size instead of the distance from the origin. Candidates are
 // compared by cross-multiplication (no division in the loop). A plane with
 // |n.d| <= 1e-6 |n||d| (grazing; FP32 cannot fix the sign of n.d) is
-// re-evaluated in FP64 from the FP32 inputs.
+// re-evaluated in FP64 from the FP32 site positions.
 //
 // Compositing (Sec. 3.2): alpha = 1 - exp(-sigma delta), w = T alpha,
 // C += w c, T *= (1 - alpha); stop once T < T_eps after compositing a cell.
@@ -34,15 +34,21 @@ enum Mode { FWD = 0, BWD = 1, TRACE = 2 };
 // (forward: more warps hide the walk's dependent loads; backward: more
 // registers for the adjoint state)
 #ifndef VT_FWD_MINB
-#define VT_FWD_MINB 3
+#define VT_FWD_MINB 4
 #endif
 #ifndef VT_BWD_MINB
-#define VT_BWD_MINB 2
+#define VT_BWD_MINB 3
 #endif
 // 1: issue a cell's texel loads before its exit search (latency overlapped,
 // more live registers); 0: after it
 #ifndef VT_TEX_EARLY
 #define VT_TEX_EARLY 0
+#endif
+// warp aggregation of gradient atomics: 0 none, 1 site/sigma gradients,
+// 2 site/sigma and texel gradients. Measured on 3M sites / 4 views: 0 is
+// fastest (atomics are ~1 ms of the backward; the shuffles cost more).
+#ifndef VT_AGG
+#define VT_AGG 0
 #endif
 
 struct Scene {
@@ -52,6 +58,12 @@ struct Scene {
   int64_t n;
   int32_t R, RR;
   unsigned long long* err;
+};
+
+// one image of a launch whose images differ in size
+struct ImgEnt {
+  int64_t first_ray, first_tile;
+  int w, h, tiles_x, pad;
 };
 
 struct RP {  // render parameters, device copy
@@ -64,12 +76,22 @@ struct RP {  // render parameters, device copy
   int max_steps;
   int64_t n_rays;
   int64_t anchor_stride;
+  // ray layout: 0 plain 1-D, 1 n_images equal images, 2 table of images
+  int layout, n_tab;
+  int64_t total_tiles;
+  ImgEnt img[VT_MAX_ANCHORS];
 };
+
+// first ray of anchor a (its origin is the anchor point)
+__device__ __forceinline__ int64_t anchor_ray(const RP& P, int a) {
+  return P.layout == 2 ? P.img[a].first_ray : (int64_t)a * P.anchor_stride;
+}
 
 struct Grad {
   float4* g_cell;
   float4* g_tex;
   const float* rgb;
+  const float* rgb_lo;  // optional residual of the forward colour
   const float* grad;
 };
 
@@ -193,6 +215,17 @@ __device__ __forceinline__ void tap_weights(const Taps& t, float w[4]) {
   w[3] = __fmul_rn(t.fx, t.fy);
 }
 
+// n.d for n = sj - si: plain FP32 when the crossing is not near grazing
+// (|n.d| > 1e-2 |n||d|, relative error < 2e-5), else the compensated form.
+__device__ __forceinline__ float exact_nd(float3 si, float3 sj, float3 d);
+__device__ __forceinline__ float crossing_nd(float3 si, float3 sj, float3 d, float dd) {
+  const float nx = __fsub_rn(sj.x, si.x), ny = __fsub_rn(sj.y, si.y), nz = __fsub_rn(sj.z, si.z);
+  const float nd = __fmaf_rn(nx, d.x, __fmaf_rn(ny, d.y, __fmul_rn(nz, d.z)));
+  const float nn = __fmaf_rn(nx, nx, __fmaf_rn(ny, ny, __fmul_rn(nz, nz)));
+  if (__fmul_rn(nd, nd) > __fmul_rn(1e-4f, __fmul_rn(nn, dd))) return nd;
+  return exact_nd(si, sj, d);
+}
+
 // Exact n.d for n = sj - si (FP32 inputs): n is split into rounded part and
 // rounding error (TwoSum), products are split by FMA (TwoProd) and summed with
 // compensation -- accurate to about FP32 rounding of the exact value even for
@@ -275,9 +308,10 @@ __device__ int greedy_nearest(const Scene& S, int cell, float3 q, int max_steps,
 // ---------------------------------------------------------------- anchors
 // Exact nearest site of each anchor point: packed (distance bits, user id)
 // atomicMin over all sites; blockIdx.y selects the anchor.
-__global__ void k_anchor_nn(Scene S, const float* __restrict__ o, int64_t stride, unsigned long long* key) {
+__global__ void k_anchor_nn(Scene S, RP P, const float* __restrict__ o, unsigned long long* key) {
   int a = blockIdx.y;
-  float3 q = make_float3(o[3 * a * stride], o[3 * a * stride + 1], o[3 * a * stride + 2]);
+  const int64_t ar = anchor_ray(P, a);
+  float3 q = make_float3(o[3 * ar], o[3 * ar + 1], o[3 * ar + 2]);
   unsigned long long best = ~0ull;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.n; i += (int64_t)gridDim.x * blockDim.x) {
     const float4 s = cell_pos(S.cell, (int)i);
@@ -292,12 +326,13 @@ __global__ void k_anchor_nn(Scene S, const float* __restrict__ o, int64_t stride
   if ((threadIdx.x & 31) == 0) atomicMin(key + a, best);
 }
 
-__global__ void k_anchor_refine(Scene S, const float* __restrict__ o, int64_t stride, int n_anchors,
+__global__ void k_anchor_refine(Scene S, RP P, const float* __restrict__ o, int n_anchors,
                                 const int32_t* __restrict__ inv, const unsigned long long* key, int32_t* cell,
                                 int max_steps) {
   int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= n_anchors) return;
-  float3 q = make_float3(o[3 * a * stride], o[3 * a * stride + 1], o[3 * a * stride + 2]);
+  const int64_t ar = anchor_ray(P, a);
+  float3 q = make_float3(o[3 * ar], o[3 * ar + 1], o[3 * ar + 2]);
   int c = inv[(int)(key[a] & 0xffffffffu)];
   bool ok = true;
   c = greedy_nearest(S, c, q, max_steps, ok);
@@ -306,17 +341,100 @@ __global__ void k_anchor_refine(Scene S, const float* __restrict__ o, int64_t st
 }
 
 // ---------------------------------------------------------------- ray mapping
-__device__ __forceinline__ int64_t ray_of_thread(const RP& P, int64_t tid) {
-  if (P.img_w <= 0) return tid < P.n_rays ? tid : -1;
-  int64_t warp = tid >> 5;
-  int lane = (int)(tid & 31);
-  int64_t img = warp / P.tiles_per_img;
-  if (img >= P.n_images) return -1;
-  int t = (int)(warp - img * P.tiles_per_img);
-  int ty = t / P.tiles_x, tx = t - ty * P.tiles_x;
-  int x = tx * 8 + (lane & 7), y = ty * 4 + (lane >> 3);
-  if (x >= P.img_w || y >= P.img_h) return -1;
-  return (img * P.img_h + y) * (int64_t)P.img_w + x;
+// thread -> ray (-1: none) and its anchor. In image layouts a warp covers a
+// 4 x 8 tile (8 columns, 4 rows) of one image.
+__device__ __forceinline__ int64_t ray_of_thread(const RP& P, int64_t tid, int& anchor) {
+  if (P.layout == 0) {
+    if (tid >= P.n_rays) return -1;
+    anchor = (int)(tid / P.anchor_stride);
+    return tid;
+  }
+  const int64_t warp = tid >> 5;
+  const int lane = (int)(tid & 31);
+  int64_t img, t, first;
+  int w, h, tiles_x;
+  if (P.layout == 1) {
+    img = warp / P.tiles_per_img;
+    if (img >= P.n_images) return -1;
+    t = warp - img * P.tiles_per_img;
+    w = P.img_w;
+    h = P.img_h;
+    tiles_x = P.tiles_x;
+    first = img * (int64_t)P.img_w * P.img_h;
+  } else {
+    if (warp >= P.total_tiles) return -1;
+    int lo = 0, hi = P.n_tab - 1;  // last image with first_tile <= warp
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (P.img[mid].first_tile <= warp)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    img = lo;
+    t = warp - P.img[lo].first_tile;
+    w = P.img[lo].w;
+    h = P.img[lo].h;
+    tiles_x = P.img[lo].tiles_x;
+    first = P.img[lo].first_ray;
+  }
+  const int ty = (int)(t / tiles_x), tx = (int)(t - (int64_t)ty * tiles_x);
+  const int x = tx * 8 + (lane & 7), y = ty * 4 + (lane >> 3);
+  if (x >= w || y >= h) return -1;
+  const int64_t ray = first + (int64_t)y * w + x;
+  anchor = P.layout == 2 ? (int)img : (int)(ray / P.anchor_stride);
+  return ray;
+}
+
+// ---------------------------------------------------------------- gradient atomics
+// Warp aggregation: lanes of `act` holding the same non-negative key combine
+// their N values pairwise (butterfly over lane ^ 1, 2, 4, 8, 16; the lower
+// lane of a matching pair keeps the sum, the upper one is zeroed); a round
+// with no matching pair anywhere is skipped. Values only move, so the sum
+// over lanes is unchanged; afterwards the lanes still holding values issue
+// the atomics.
+template <int N>
+__device__ __forceinline__ void warp_combine(unsigned act, int key, float (&v)[N]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int ko = __shfl_xor_sync(act, key, off);
+    const bool same = ((act >> (lane ^ off)) & 1u) && ko == key && key >= 0;
+    if (__any_sync(act, same)) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const float vo = __shfl_xor_sync(act, v[i], off);
+        if (same) v[i] = (lane & off) ? 0.f : v[i] + vo;
+      }
+    }
+  }
+}
+
+// dL/d(site, sigma) of cell c += (gx, gy, gz, gsig)
+__device__ __forceinline__ void add_cell_grad(float4* g_cell, int c, float gx, float gy, float gz, float gsig) {
+#if VT_AGG >= 1
+  float v[4] = {gx, gy, gz, gsig};
+  warp_combine<4>(__activemask(), c, v);
+  if (v[0] != 0.f || v[1] != 0.f || v[2] != 0.f || v[3] != 0.f) atomicAdd(g_cell + c, make_float4(v[0], v[1], v[2], v[3]));
+#else
+  atomicAdd(g_cell + c, make_float4(gx, gy, gz, gsig));
+#endif
+}
+
+// texel gradients of the four bilinear taps: g * w * tap weight
+__device__ __forceinline__ void add_tex_grad(float4* g_tex, int64_t b0, int sx, int sy, float g0, float g1, float g2,
+                                             float w, const float (&tw)[4], bool agg) {
+  const float a0 = w * tw[0], a1 = w * tw[1], a2 = w * tw[2], a3 = w * tw[3];
+  float v[12] = {g0 * a0, g1 * a0, g2 * a0, g0 * a1, g1 * a1, g2 * a1,
+                 g0 * a2, g1 * a2, g2 * a2, g0 * a3, g1 * a3, g2 * a3};
+#if VT_AGG >= 2
+  if (agg) warp_combine<12>(__activemask(), (int)b0, v);
+#endif
+  const int64_t e[4] = {b0, b0 + sx, b0 + sy, b0 + sx + sy};
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (v[3 * q] != 0.f || v[3 * q + 1] != 0.f || v[3 * q + 2] != 0.f)
+      atomicAdd(g_tex + e[q], make_float4(v[3 * q], v[3 * q + 1], v[3 * q + 2], 0.f));
 }
 
 // ---------------------------------------------------------------- the walk
@@ -340,7 +458,8 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
     k_walk(Scene S, RP P, const float* __restrict__ O, const float* __restrict__ D,
            const int32_t* __restrict__ anchor_cell, float* __restrict__ rgb_out, float* __restrict__ T_out,
            int32_t* __restrict__ steps_out, Grad G, Trace TR) {
-  const int64_t ray = ray_of_thread(P, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+  int anchor = 0;
+  const int64_t ray = ray_of_thread(P, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, anchor);
   if (ray < 0) return;
   const float3 o = make_float3(O[3 * ray], O[3 * ray + 1], O[3 * ray + 2]);
   const float3 d = make_float3(D[3 * ray], D[3 * ray + 1], D[3 * ray + 2]);
@@ -370,7 +489,7 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
     atomicOr(S.err, (unsigned long long)VT_EBIT_BAD_RAY);
   } else if (t1 > t0) {
     const Taps tp = taps_for(d, S.R);
-    const float G2dd = __fmul_rn(1e-12f, dd);  // grazing: (n.d)^2 <= 1e-12 |n|^2 |d|^2
+    const float Gd = __fmul_rn(1e-6f, sqrtf(dd));  // grazing scale 1e-6 |d|
     // BWD: g = dL/dC and the suffix S_k = C_out - sum_{m<=k} w_m c_m as float-float
     float g0 = 0.f, g1 = 0.f, g2 = 0.f, Sh0 = 0.f, Sh1 = 0.f, Sh2 = 0.f, Sl0 = 0.f, Sl1 = 0.f, Sl2 = 0.f;
     if (MODE == BWD) {
@@ -380,14 +499,18 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
       Sh0 = G.rgb[3 * ray];
       Sh1 = G.rgb[3 * ray + 1];
       Sh2 = G.rgb[3 * ray + 2];
+      if (G.rgb_lo) {
+        Sl0 = G.rgb_lo[3 * ray];
+        Sl1 = G.rgb_lo[3 * ray + 1];
+        Sl2 = G.rgb_lo[3 * ray + 2];
+      }
     }
     // start cell: the anchor's cell if the origin is the anchor point, else a
     // greedy walk from it to the origin
     int cell;
     {
-      const int64_t a = ray / P.anchor_stride;
-      const int64_t ar = a * P.anchor_stride;
-      cell = anchor_cell[a];
+      const int64_t ar = anchor_ray(P, anchor);
+      cell = anchor_cell[anchor];
       if (O[3 * ar] != o.x || O[3 * ar + 1] != o.y || O[3 * ar + 2] != o.z) {
         bool ok = true;
         cell = greedy_nearest(S, cell, o, P.max_steps, ok);
@@ -421,15 +544,19 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
       }
       const float3 r = rel_pos(si, o, d, th, tl);
       // ---- exit search over the Delaunay neighbours (offset records n = s_j - s_i)
+      // grazing bound for this cell: |n.d| <= 1e-6 |d| max_j |n_j| (a superset
+      // of the planes with |n.d| <= 1e-6 |n||d|)
+      const float Gc = __fmul_rn(Gd, __int_as_float(m.w));
       float bn = 1.f, bd = 0.f;  // best dt = bn / bd (bd == 0: none yet)
       int bj = -1;
 #pragma unroll 2
       for (int p = m.x; p < m.y; ++p) {
         const float4 q = __ldg(S.nbr + p);
         float den = __fmaf_rn(q.x, d.x, __fmaf_rn(q.y, d.y, __fmul_rn(q.z, d.z)));
-        const float nn = __fmaf_rn(q.x, q.x, __fmaf_rn(q.y, q.y, __fmul_rn(q.z, q.z)));
-        float num = __fmaf_rn(q.x, r.x, __fmaf_rn(q.y, r.y, __fmaf_rn(q.z, r.z, __fmul_rn(0.5f, nn))));
-        if (__fmul_rn(den, den) <= __fmul_rn(G2dd, nn)) {
+        // n.(r + n/2)
+        float num = __fmaf_rn(q.x, __fmaf_rn(0.5f, q.x, r.x),
+                              __fmaf_rn(q.y, __fmaf_rn(0.5f, q.y, r.y), __fmul_rn(q.z, __fmaf_rn(0.5f, q.z, r.z))));
+        if (fabsf(den) <= Gc) {
           // grazing plane: FP64 recheck from the FP32 inputs
           atomicAdd(S.err + 1, 1ull);
           if (!grazing_fp64(S.cell, __float_as_int(q.w), si, o, d, th, tl, &num)) continue;
@@ -450,7 +577,7 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
         tx2 = load_texel<DT>(S.tex, tb0 + tp.sy);
         tx3 = load_texel<DT>(S.tex, tb0 + tp.sx + tp.sy);
       }
-      const float dt = bj >= 0 ? __fdiv_rn(bn, bd) : INFINITY;
+      const float dt = bj >= 0 ? __fdividef(bn, bd) : INFINITY;
       float eh = th, el = tl;  // exit parameter
       if (bj >= 0)
         ff_add(eh, el, dt);
@@ -480,7 +607,7 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
       bool coloured = false;
       float tw[4];
       if (delta > 0.f) {
-        const float e = expf(-__fmul_rn(sig, delta));
+        const float e = __expf(-__fmul_rn(sig, delta));
         const float alpha = __fsub_rn(1.f, e);
         w = __fmul_rn(T, alpha);
         const float Tn = __fmul_rn(T, e);
@@ -514,23 +641,17 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
         // dL/dt_b = sigma_prev dtau_prev - sigma dtau; x_b - s_prev = n - r, s_cur - x_b = r
         float3 gs = make_float3(0.f, 0.f, 0.f);
         if (pc >= 0 && cross_valid) {
-          const float nd = exact_nd(p_s, si, d);
-          const float dtb = (p_sdtau - sig * dtau) / nd;
+          const float nd = crossing_nd(p_s, si, d, dd);
+          const float dtb = __fdividef(p_sdtau - sig * dtau, nd);
           const float nx = __fsub_rn(si.x, p_s.x), ny = __fsub_rn(si.y, p_s.y), nz = __fsub_rn(si.z, p_s.z);
           p_gs.x += dtb * (nx - r.x);
           p_gs.y += dtb * (ny - r.y);
           p_gs.z += dtb * (nz - r.z);
           gs = make_float3(dtb * r.x, dtb * r.y, dtb * r.z);
         }
-        if (pc >= 0 && (p_gs.x != 0.f || p_gs.y != 0.f || p_gs.z != 0.f || p_gsig != 0.f))
-          atomicAdd(G.g_cell + pc, make_float4(p_gs.x, p_gs.y, p_gs.z, p_gsig));
-        if (coloured && w > 0.f) {
-          const float ww0 = w * tw[0], ww1 = w * tw[1], ww2 = w * tw[2], ww3 = w * tw[3];
-          if (ww0 != 0.f) atomicAdd(G.g_tex + tb0, make_float4(g0 * ww0, g1 * ww0, g2 * ww0, 0.f));
-          if (ww1 != 0.f) atomicAdd(G.g_tex + tb0 + tp.sx, make_float4(g0 * ww1, g1 * ww1, g2 * ww1, 0.f));
-          if (ww2 != 0.f) atomicAdd(G.g_tex + tb0 + tp.sy, make_float4(g0 * ww2, g1 * ww2, g2 * ww2, 0.f));
-          if (ww3 != 0.f) atomicAdd(G.g_tex + tb0 + tp.sx + tp.sy, make_float4(g0 * ww3, g1 * ww3, g2 * ww3, 0.f));
-        }
+        if (pc >= 0) add_cell_grad(G.g_cell, pc, p_gs.x, p_gs.y, p_gs.z, p_gsig);
+        if (coloured && w > 0.f)
+          add_tex_grad(G.g_tex, tb0, tp.sx, tp.sy, g0, g1, g2, w, tw, S.n * S.RR < ((int64_t)1 << 31));
         pc = cell;
         p_sdtau = sig * dtau;
         p_gsig = dtau * delta;
@@ -543,13 +664,13 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
           const float4 q4 = cell_pos(S.cell, bj);
           const float3 sj = make_float3(q4.x, q4.y, q4.z);
           const float3 re = rel_pos(si, o, d, eh, el);  // s_K - x_out
-          const float nd = exact_nd(si, sj, d);
-          const float dtb = p_sdtau / nd;
+          const float nd = crossing_nd(si, sj, d, dd);
+          const float dtb = __fdividef(p_sdtau, nd);
           const float nx = __fsub_rn(sj.x, si.x), ny = __fsub_rn(sj.y, si.y), nz = __fsub_rn(sj.z, si.z);
           p_gs.x -= dtb * re.x;
           p_gs.y -= dtb * re.y;
           p_gs.z -= dtb * re.z;
-          atomicAdd(G.g_cell + bj, make_float4(dtb * (re.x + nx), dtb * (re.y + ny), dtb * (re.z + nz), 0.f));
+          add_cell_grad(G.g_cell, bj, dtb * (re.x + nx), dtb * (re.y + ny), dtb * (re.z + nz), 0.f);
         }
       }
       if (stop || exit_beyond) break;
@@ -557,8 +678,7 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
       th = eh;
       tl = el;
     }
-    if (MODE == BWD && pc >= 0 && (p_gs.x != 0.f || p_gs.y != 0.f || p_gs.z != 0.f || p_gsig != 0.f))
-      atomicAdd(G.g_cell + pc, make_float4(p_gs.x, p_gs.y, p_gs.z, p_gsig));
+    if (MODE == BWD && pc >= 0) add_cell_grad(G.g_cell, pc, p_gs.x, p_gs.y, p_gs.z, p_gsig);
     if (MODE == FWD) {
       ff_fma_acc(Ch0, Cl0, T, P.bg.x, 1.f);
       ff_fma_acc(Ch1, Cl1, T, P.bg.y, 1.f);
@@ -570,9 +690,16 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
     Ch2 = P.bg.z;
   }
   if (MODE == FWD) {
-    rgb_out[3 * ray] = __fadd_rn(Ch0, Cl0);
-    rgb_out[3 * ray + 1] = __fadd_rn(Ch1, Cl1);
-    rgb_out[3 * ray + 2] = __fadd_rn(Ch2, Cl2);
+    const float r0 = __fadd_rn(Ch0, Cl0), r1 = __fadd_rn(Ch1, Cl1), r2 = __fadd_rn(Ch2, Cl2);
+    rgb_out[3 * ray] = r0;
+    rgb_out[3 * ray + 1] = r1;
+    rgb_out[3 * ray + 2] = r2;
+    if (G.rgb_lo) {  // forward: residual output (C - rounded C), Fast2Sum
+      float* lo = const_cast<float*>(G.rgb_lo);
+      lo[3 * ray] = __fsub_rn(Cl0, __fsub_rn(r0, Ch0));
+      lo[3 * ray + 1] = __fsub_rn(Cl1, __fsub_rn(r1, Ch1));
+      lo[3 * ray + 2] = __fsub_rn(Cl2, __fsub_rn(r2, Ch2));
+    }
     if (T_out) T_out[ray] = T;
     if (steps_out) steps_out[ray] = k;
   } else if (MODE == TRACE) {
@@ -627,7 +754,36 @@ vt_status make_rp(const vt_scene* s, int64_t n_rays, const vt_render_params* p, 
   P.max_steps = (int)ms;
   if (!(p->t_far >= p->t_near) || !isfinite(p->t_near) || !(p->T_eps >= 0.f)) return VT_ERR_INVALID_ARG;
   int64_t per_image;
+  P.layout = 0;
+  P.n_tab = 0;
+  P.total_tiles = 0;
+  if (p->image_sizes) {
+    // images of different sizes, one anchor each
+    if (p->n_images <= 0 || p->n_images > VT_MAX_ANCHORS) return VT_ERR_INVALID_ARG;
+    int64_t ray0 = 0, tile0 = 0;
+    for (int i = 0; i < p->n_images; ++i) {
+      const int w = p->image_sizes[2 * i], h = p->image_sizes[2 * i + 1];
+      if (w <= 0 || h <= 0) return VT_ERR_INVALID_ARG;
+      ImgEnt& e = P.img[i];
+      e.first_ray = ray0;
+      e.first_tile = tile0;
+      e.w = w;
+      e.h = h;
+      e.tiles_x = (w + 7) / 8;
+      e.pad = 0;
+      ray0 += (int64_t)w * h;
+      tile0 += (int64_t)e.tiles_x * ((h + 3) / 4);
+    }
+    if (ray0 != n_rays) return VT_ERR_INVALID_ARG;
+    P.layout = 2;
+    P.n_tab = p->n_images;
+    P.total_tiles = tile0;
+    P.tiles_x = P.tiles_per_img = 0;
+    P.anchor_stride = 1;
+    return VT_OK;
+  }
   if (p->img_w > 0) {
+    P.layout = 1;
     if (p->img_h <= 0 || p->n_images <= 0) return VT_ERR_INVALID_ARG;
     per_image = (int64_t)p->img_w * p->img_h;
     if (per_image * p->n_images != n_rays) return VT_ERR_INVALID_ARG;
@@ -644,8 +800,14 @@ vt_status make_rp(const vt_scene* s, int64_t n_rays, const vt_render_params* p, 
 }
 
 int64_t walk_threads(const RP& P) {
-  if (P.img_w <= 0) return P.n_rays;
+  if (P.layout == 0) return P.n_rays;
+  if (P.layout == 2) return P.total_tiles * 32;
   return (int64_t)P.n_images * P.tiles_per_img * 32;
+}
+
+int n_anchors(const RP& P) {
+  if (P.layout == 2) return P.n_tab;
+  return (int)((P.n_rays + P.anchor_stride - 1) / P.anchor_stride);
 }
 
 Scene scene_view(vt_scene* s) {
@@ -661,12 +823,12 @@ Scene scene_view(vt_scene* s) {
 }
 
 vt_status anchors(vt_scene* s, const Scene& S, const RP& P, const float* o, cudaStream_t st) {
-  int na = (int)((P.n_rays + P.anchor_stride - 1) / P.anchor_stride);
+  const int na = n_anchors(P);
   if (na < 1 || na > VT_MAX_ANCHORS) return VT_ERR_INVALID_ARG;
   VT_CUDA_TRY(cudaMemsetAsync(s->anchor_key, 0xff, na * sizeof(unsigned long long), st));
   dim3 g(vt_grid(s->n, 256, 152 * 2), na);
-  k_anchor_nn<<<g, 256, 0, st>>>(S, o, P.anchor_stride, s->anchor_key);
-  k_anchor_refine<<<1, 64, 0, st>>>(S, o, P.anchor_stride, na, s->inv, s->anchor_key, s->anchor_cell, P.max_steps);
+  k_anchor_nn<<<g, 256, 0, st>>>(S, P, o, s->anchor_key);
+  k_anchor_refine<<<1, 64, 0, st>>>(S, P, o, na, s->inv, s->anchor_key, s->anchor_cell, P.max_steps);
   VT_CUDA_TRY(cudaGetLastError());
   return VT_OK;
 }
@@ -693,7 +855,7 @@ extern "C" {
 
 vt_status vt_render_fwd(vt_scene* s, int64_t n_rays, const float* o, const float* d, const float* time,
                         const vt_render_params* p, float* rgb_out, float* T_out, int32_t* steps_out,
-                        void* stream) {
+                        float* rgb_residual, void* stream) {
   (void)time;
   if (!s || n_rays < 0 || (n_rays > 0 && (!o || !d || !rgb_out))) return VT_ERR_INVALID_ARG;
   if (n_rays == 0) return VT_OK;
@@ -704,12 +866,15 @@ vt_status vt_render_fwd(vt_scene* s, int64_t n_rays, const float* o, const float
   Scene S = scene_view(s);
   r = anchors(s, S, P, o, st);
   if (r != VT_OK) return r;
-  return launch_walk<FWD>(s, S, P, o, d, rgb_out, T_out, steps_out, Grad{}, Trace{}, st);
+  Grad G{};
+  G.rgb_lo = rgb_residual;
+  return launch_walk<FWD>(s, S, P, o, d, rgb_out, T_out, steps_out, G, Trace{}, st);
 }
 
 vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float* d, const float* time,
-                        const vt_render_params* p, const float* rgb_out, const float* grad_rgb, float* grad_sites,
-                        float* grad_sigma, float* grad_tex, void* stream) {
+                        const vt_render_params* p, const float* rgb_out, const float* rgb_residual,
+                        const float* grad_rgb, float* grad_sites, float* grad_sigma, float* grad_tex,
+                        void* stream) {
   (void)time;
   if (!s || n_rays < 0 || (n_rays > 0 && (!o || !d || !rgb_out || !grad_rgb))) return VT_ERR_INVALID_ARG;
   RP P;
@@ -725,7 +890,7 @@ vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float
   if (n_rays > 0) {
     r = anchors(s, S, P, o, st);
     if (r != VT_OK) return r;
-    Grad G{s->g_cell, s->g_tex, rgb_out, grad_rgb};
+    Grad G{s->g_cell, s->g_tex, rgb_out, rgb_residual, grad_rgb};
     r = launch_walk<BWD>(s, S, P, o, d, nullptr, nullptr, nullptr, G, Trace{}, st);
     if (r != VT_OK) return r;
   }
@@ -813,7 +978,7 @@ vt_status vt_render_bwd_static(vt_scene* s, int64_t n_rays, const float* o, cons
   if (n_rays > 0) {
     r = anchors(s, S, P, o, st);
     if (r != VT_OK) return r;
-    Grad G{g_cell, g_tex, rgb_out, grad_rgb};
+    Grad G{g_cell, g_tex, rgb_out, nullptr, grad_rgb};
     r = launch_walk<BWD>(s, S, P, o, d, nullptr, nullptr, nullptr, G, Trace{}, st);
     if (r != VT_OK) return r;
   }

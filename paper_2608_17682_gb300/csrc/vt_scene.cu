@@ -175,6 +175,19 @@ __global__ void k_fill_nbr(int64_t n, const vt_cell* __restrict__ cell, const in
   }
 }
 
+// largest neighbour offset |n| of each cell (bound for the grazing test)
+__global__ void k_cell_nmax(int64_t n, vt_cell* __restrict__ cell, const float4* __restrict__ nbr) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int b = cell[i].beg, e = cell[i].end;
+    float m = 0.f;
+    for (int p = b; p < e; ++p) {
+      const float4 q = nbr[p];
+      m = fmaxf(m, sqrtf(q.x * q.x + q.y * q.y + q.z * q.z));
+    }
+    cell[i].pad = __float_as_int(m * 1.0001f);
+  }
+}
+
 // texel packing: [N,R,R,3] FP32 user order -> Morton-ordered RGBA in storage dtype
 template <int DT>
 __global__ void k_pack_tex(int64_t n, int32_t RR, const int32_t* __restrict__ perm, const float* __restrict__ tex,
@@ -323,8 +336,13 @@ vt_status create_impl(const vt_scene_desc* dsc, cudaStream_t st, vt_scene* s) {
       rs = VT_ERR_OOM;
       break;
     }
-    if (cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, code, code2, ids, s->perm, (int)n, 0, 63, st) !=
-        cudaSuccess) {
+    if (dsc->flags & VT_SCENE_KEEP_ORDER) {
+      if (cudaMemcpyAsync(s->perm, ids, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+        rs = VT_ERR_CUDA;
+        break;
+      }
+    } else if (cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, code, code2, ids, s->perm, (int)n, 0, 63, st) !=
+               cudaSuccess) {
       rs = VT_ERR_CUDA;
       break;
     }
@@ -336,6 +354,7 @@ vt_status create_impl(const vt_scene_desc* dsc, cudaStream_t st, vt_scene* s) {
     }
     k_fill_cells<<<g, 256, 0, st>>>(n, s->perm, dsc->sites, dsc->sigma, beg, deg, s->cell, 0);
     k_fill_nbr<<<g, 256, 0, st>>>(n, s->cell, dsc->adj_offsets, dsc->adj_indices, s->inv, s->nbr);
+    k_cell_nmax<<<g, 256, 0, st>>>(n, s->cell, s->nbr);
     rs = pack_tex(s, dsc->tex, st);
     if (rs != VT_OK) break;
     if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) rs = VT_ERR_CUDA;
@@ -409,7 +428,10 @@ vt_status vt_scene_update(vt_scene* s, const float* sites, const float* sigma, c
     if (v != VT_OK) return v;
     int g = vt_grid(s->n, 256, 152 * 32);
     k_fill_cells<<<g, 256, 0, st>>>(s->n, s->perm, sites, sigma, nullptr, nullptr, s->cell, 1);
-    if (sites) k_refresh_nbr<<<g, 256, 0, st>>>(s->n, s->cell, s->nbr);
+    if (sites) {
+      k_refresh_nbr<<<g, 256, 0, st>>>(s->n, s->cell, s->nbr);
+      k_cell_nmax<<<g, 256, 0, st>>>(s->n, s->cell, s->nbr);
+    }
     VT_CUDA_TRY(cudaGetLastError());
   }
   if (tex) {

@@ -325,6 +325,25 @@ def crop_scene(sites_all, sigma_all, tex_all, lo, hi) -> Scene:
     return Scene(s, np.ascontiguousarray(sigma_all[m]), np.ascontiguousarray(tex_all[m]), off, idx)
 
 
+def surface_crop(n_max: int = 1000, side: float = 0.3, R: int = 8, seed: int = 1003) -> Scene:
+    """About n_max sites of the surface-concentrated distribution (generated
+    at 1M sites) inside a side^3 box centred on a surface site, with sigma by
+    the same rule, fresh U[0,1] textures and their own Delaunay graph -- the
+    small scene of the gradient finite-difference checks."""
+    rng = np.random.default_rng(seed)
+    pts, surf = surface_sites(1_000_000, rng)
+    sigma = np.where(surf, np.exp(rng.normal(3.0, 1.0, size=len(pts))), np.exp(rng.normal(-2.0, 1.0, size=len(pts))))
+    c = pts[np.nonzero(surf & (np.abs(pts).max(axis=1) < 0.5))[0][0]].astype(np.float64)
+    m = np.all(np.abs(pts - c) <= side / 2, axis=1)
+    idx = np.nonzero(m)[0]
+    if len(idx) > n_max:
+        idx = np.sort(rng.choice(idx, size=n_max, replace=False))
+    sites = np.ascontiguousarray(pts[idx])
+    off, ind = delaunay_csr(sites, cache=False)
+    tex = textures(len(sites), R, rng)
+    return Scene(sites, sigma[idx].astype(np.float32), tex, off, ind)
+
+
 def default_params(**kw):
     p = dict(t_near=0.0, t_far=20.0, use_clip_box=False, clip_lo=(0.0, 0.0, 0.0), clip_hi=(1.0, 1.0, 1.0),
              T_eps=1e-4, skip_weight=0.0, bg=(1.0, 1.0, 1.0))

@@ -43,6 +43,13 @@ def to_dev(*a):
     return [torch.as_tensor(x, device=DEV).contiguous() for x in a]
 
 
+def fwd_res(scene, to, td, P):
+    """Forward render that also returns the colour residual for the backward."""
+    res = torch.empty(to.shape[0], 3, device=DEV)
+    rgb = api.render_fwd(scene, to, td, P, residual=res)[0]
+    return rgb, res
+
+
 def compare_sequences(gc, gn, oc, on, flags):
     """Cell sequences equal for every unflagged ray; returns (#checked, #flagged-mismatch)."""
     ok = (flags & O.BAND_FLAGS) == 0
@@ -189,8 +196,8 @@ def test_tiny_backward_parity(tiny):
     g = np.random.default_rng(5).normal(size=(len(o), 3)) * ok[:, None]  # flagged rays carry no gradient
     scene = api.Scene.from_workload(sc)
     to, td, tg = to_dev(o, d, g.astype(np.float32))
-    rgb = api.render_fwd(scene, to, td, P)[0]
-    gs, gsig, gt = api.render_bwd(scene, to, td, P, rgb, tg)
+    rgb, res = fwd_res(scene, to, td, P)
+    gs, gsig, gt = api.render_bwd(scene, to, td, P, rgb, tg, residual=res)
     assert scene.get_error()[0] == 0
     ogs, ogsig, ogt = O.render_bwd(osc, o, d, g.astype(np.float32).astype(np.float64),
                                    params=oracle_params(wl.params))
@@ -209,8 +216,8 @@ def test_medium_backward_parity(medium):
     g = (np.random.default_rng(6).normal(size=(len(o), 3)) * ok[:, None]).astype(np.float32)
     scene = api.Scene.from_workload(sc)
     to, td, tg = to_dev(o, d, g)
-    rgb = api.render_fwd(scene, to, td, P)[0]
-    gs, gsig, gt = api.render_bwd(scene, to, td, P, rgb, tg)
+    rgb, res = fwd_res(scene, to, td, P)
+    gs, gsig, gt = api.render_bwd(scene, to, td, P, rgb, tg, residual=res)
     ogs, ogsig, ogt = O.render_bwd(osc, o, d, g.astype(np.float64), params=oracle_params(base))
     grad_close(gsig.cpu().numpy(), ogsig, "sigma")
     grad_close(gt.cpu().numpy(), ogt, "tex")
@@ -403,7 +410,8 @@ def test_wide_angle_moving_origin_rays(medium):
     base = W.default_params()
     scene = api.Scene.from_workload(sc, tex_dtype="f16")
     to, td = to_dev(o, d)
-    rgb, T, steps = api.render_fwd(scene, to, td, gpu_params(base))
+    res = torch.empty(to.shape[0], 3, device=DEV)
+    rgb, T, steps = api.render_fwd(scene, to, td, gpu_params(base), residual=res)
     cells, _, n_cells = api.trace_cells(scene, to, td, gpu_params(base), max_cells=400)
     assert scene.get_error()[0] == 0
     tq = torch.as_tensor(sc.tex).half().float().numpy()
@@ -415,8 +423,95 @@ def test_wide_angle_moving_origin_rays(medium):
     assert np.abs(rgb.cpu().numpy()[ok] - orgb[ok]).max() <= IMG_TOL
     assert np.array_equal(steps.cpu().numpy()[ok], osteps[ok])
     g = (np.random.default_rng(80).normal(size=(len(o), 3)) * ok[:, None]).astype(np.float32)
-    gs, gsig, gt = api.render_bwd(scene, to, td, gpu_params(base), rgb, torch.as_tensor(g, device=DEV))
+    gs, gsig, gt = api.render_bwd(scene, to, td, gpu_params(base), rgb, torch.as_tensor(g, device=DEV), residual=res)
     ogs, ogsig, ogt = O.render_bwd(osq, o, d, g.astype(np.float64), params=oracle_params(base))
     grad_close(gsig.cpu().numpy(), ogsig, "sigma")
     grad_close(gt.cpu().numpy(), ogt, "tex")
     grad_close(gs.cpu().numpy(), ogs, "sites")
+
+
+def test_image_table_layout_matches_1d(medium):
+    """Images of different sizes in one launch (image table, 4x8 tiles per
+    image, one anchor per image) give the same per-ray results as 1-D order."""
+    sc, osc, o_, d_, cams = medium
+    base = W.default_params()
+    sizes = [(64, 64), (203, 31), (40, 8), (13, 5)]
+    rng = np.random.default_rng(81)
+    os_, ds = [], []
+    for k, (w, h) in enumerate(sizes):
+        eye = W.orbit_eye(np.zeros(3), 3.0, 40.0 * k, 20.0)
+        o, d = W.frustum_rays(eye, np.zeros(3), w, h, rng, origin_jitter=0.002 * k)
+        os_.append(o)
+        ds.append(d)
+    to, td = to_dev(np.concatenate(os_), np.concatenate(ds))
+    scene = api.Scene.from_workload(sc, tex_dtype="f16")
+    a = api.render_fwd(scene, to, td, gpu_params(base, image_sizes=sizes))
+    b = api.render_fwd(scene, to, td, gpu_params(base))
+    assert scene.get_error()[0] == 0
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    g = torch.randn(to.shape[0], 3, device=DEV)
+    ga = api.render_bwd(scene, to, td, gpu_params(base, image_sizes=sizes), a[0], g)
+    gb = api.render_bwd(scene, to, td, gpu_params(base), b[0], g)
+    for x, y in zip(ga, gb):
+        assert (x - y).abs().max().item() <= 1e-5 * max(1.0, y.abs().max().item())
+
+
+def test_mixed_cameras_one_launch(medium):
+    """Pinhole, fisheye, rolling-shutter and thin-lens views generated on the
+    GPU and rendered in one launch; per-ray results equal a 1-D launch, and
+    the 4-sample thin-lens pixels average correctly."""
+    sc, osc, o_, d_, cams = medium
+    o0 = np.zeros(3)
+    mk = [W.look_at_camera(0, 48, 32, W.orbit_eye(o0, 3.0, 10, 20), o0),
+          W.look_at_camera(1, 48, 32, W.orbit_eye(o0, 3.0, 100, 20), o0),
+          W.look_at_camera(2, 48, 32, W.orbit_eye(o0, 3.0, 190, 20), o0, rs_velocity=(0.05, 0.0, 0.0)),
+          W.look_at_camera(3, 48, 32, W.orbit_eye(o0, 3.0, 280, 20), o0, lens_radius=0.01, focus_dist=3.0,
+                           lens_samples=4, seed=7)]
+    o, d, t = api.generate_rays(mk)
+    sizes = [(48 * (4 if c.kind == 3 else 1), 32) for c in mk]
+    base = W.default_params()
+    scene = api.Scene.from_workload(sc)
+    a = api.render_fwd(scene, o, d, gpu_params(base, image_sizes=sizes), time=t)
+    b = api.render_fwd(scene, o, d, gpu_params(base))
+    assert scene.get_error()[0] == 0
+    assert torch.equal(a[0], b[0]) and torch.equal(a[2], b[2])
+    n_px = 48 * 32
+    lens = a[0][3 * n_px:]
+    px = api.average_samples(lens.contiguous(), 4)
+    assert torch.allclose(px, lens.view(n_px, 4, 3).mean(1), atol=1e-6)
+
+
+def test_keep_order_scene_gives_identical_results(medium):
+    """Cell storage order (Morton vs user order) changes memory locality only:
+    every decision and value is the same."""
+    sc, osc, o, d, cams = medium
+    P = gpu_params(W.default_params(), img_w=203, img_h=121, n_images=2)
+    to, td = to_dev(o, d)
+    a = api.render_fwd(api.Scene.from_workload(sc), to, td, P)
+    b = api.render_fwd(api.Scene.from_workload(sc, keep_order=True), to, td, P)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
+def test_gradients_vs_finite_differences_on_surface_crop():
+    """GPU (FP32) gradients on the 1,000-site crop against FP64 central finite
+    differences of the oracle's forward pass, at 1e-3 relative."""
+    from test_oracle_pins import crop_setup, fd_crop
+    sc, o, d, Y, params = crop_setup()
+    res, (gs_o, gsig_o, gt_o) = fd_crop(sc, o, d, Y, params)
+    scene = api.Scene.from_workload(sc)
+    P = gpu_params(params, img_w=32, img_h=32, n_images=1)
+    to, td = to_dev(o.astype(np.float32), d.astype(np.float32))
+    rgb, resid = fwd_res(scene, to, td, P)
+    # dL/dC from the oracle's colours, so both sides differentiate the same L
+    osc = O.OracleScene.from_workload_scene(sc)
+    orgb = O.render(osc, o, d, params=O.make_params(**params))[0]
+    g = torch.as_tensor((orgb - Y).astype(np.float32), device=DEV)
+    gs, gsig, gt = [x.cpu().numpy() for x in api.render_bwd(scene, to, td, P, rgb, g, residual=resid)]
+    got = {"sigma": gsig, "tex": gt, "sites": gs}
+    floors = {"sigma": 1e-3 * np.abs(gsig_o).max(), "tex": 1e-3 * np.abs(gt_o).max(),
+              "sites": 1e-3 * np.abs(gs_o).max()}
+    for kind, idx, fd, an in res:
+        v = got[kind][idx]
+        assert abs(v - fd) <= GRAD_REL * max(abs(fd), floors[kind]), (kind, idx, v, fd)

@@ -47,7 +47,8 @@ def test_fullsize_forward_and_backward(big, dtype):
     scene = api.Scene.from_workload(sc, tex_dtype=dtype)
     to = torch.as_tensor(o, device="cuda")
     td = torch.as_tensor(d, device="cuda")
-    rgb, T, steps = api.render_fwd(scene, to, td, P)
+    res = torch.empty(len(o), 3, device="cuda")
+    rgb, T, steps = api.render_fwd(scene, to, td, P, residual=res)
     assert scene.get_error()[0] == 0
     tex = sc.tex if dtype == "f32" else torch.as_tensor(sc.tex).half().float().numpy()
     osc = O.OracleScene(sc.sites, sc.sigma, tex, sc.offsets, sc.indices)
@@ -73,7 +74,7 @@ def test_fullsize_forward_and_backward(big, dtype):
     g = np.zeros((len(o), 3), np.float32)
     rng = np.random.default_rng(12)
     g[sel[ok]] = rng.normal(size=(ok.sum(), 3))
-    gs, gsig, gt = api.render_bwd(scene, to, td, P, rgb, torch.as_tensor(g, device="cuda"))
+    gs, gsig, gt = api.render_bwd(scene, to, td, P, rgb, torch.as_tensor(g, device="cuda"), residual=res)
     assert scene.get_error()[0] == 0
     ogs, ogsig, ogt = O.render_bwd(osc, o[sel], d[sel], g[sel].astype(np.float64), params=op)
     grad_close(gsig.cpu().numpy(), ogsig, "sigma")

@@ -50,11 +50,11 @@ def test_host_argument_validation(vt):
     out = C.c_void_p(123)
     assert vt.lib.vt_scene_create(None, None, C.byref(out)) == vt.VT_ERR_INVALID_ARG
     assert out.value is None
-    d = vt.vt_scene_desc(0, 4, 0, 0, 0, 0, 0, 0)
+    d = vt.vt_scene_desc(0, 4, 0, 0, 0, 0, 0, 0, 0)
     assert vt.lib.vt_scene_create(C.byref(d), None, C.byref(out)) == vt.VT_ERR_INVALID_ARG
-    d = vt.vt_scene_desc(10, 1, 0, 8, 8, 8, 8, 8)  # tex_res < 2
+    d = vt.vt_scene_desc(10, 1, 0, 8, 8, 8, 8, 8, 0)  # tex_res < 2
     assert vt.lib.vt_scene_create(C.byref(d), None, C.byref(out)) == vt.VT_ERR_INVALID_ARG
-    d = vt.vt_scene_desc(10, 4, 7, 8, 8, 8, 8, 8)  # bad dtype
+    d = vt.vt_scene_desc(10, 4, 7, 8, 8, 8, 8, 8, 0)  # bad dtype
     assert vt.lib.vt_scene_create(C.byref(d), None, C.byref(out)) == vt.VT_ERR_INVALID_ARG
     cam = vt.vt_camera()
     cam.kind, cam.w, cam.h = 3, 4, 4
@@ -65,7 +65,7 @@ def test_host_argument_validation(vt):
     assert vt.lib.vt_generate_rays(arr, 1, C.c_void_p(8), C.c_void_p(8), None, None) == vt.VT_ERR_INVALID_ARG
     cam.lens_samples = 4
     assert vt.vt_camera_n_rays(cam) == 64
-    assert vt.lib.vt_render_fwd(None, 1, None, None, None, None, None, None, None, None) == vt.VT_ERR_INVALID_ARG
+    assert vt.lib.vt_render_fwd(None, 1, None, None, None, None, None, None, None, None, None) == vt.VT_ERR_INVALID_ARG
     assert vt.lib.vt_l2_loss(-1, None, None, None, None, None) == vt.VT_ERR_INVALID_ARG
     assert vt.lib.vt_average_samples(4, 0, None, None, None) == vt.VT_ERR_INVALID_ARG
 

@@ -568,3 +568,81 @@ def test_thin_lens_focus():
         sx, sy = s_ % 2, s_ // 2
         assert np.all(np.sign(lx[:, s_]) == (1 if sx else -1))
         assert np.all(np.sign(ly[:, s_]) == (1 if sy else -1))
+
+
+# ---------------------------------------------------------------- the 1,000-site crop (surface distribution)
+
+def crop_setup():
+    sc = W.surface_crop()
+    lo, hi = sc.sites.min(0).astype(np.float64), sc.sites.max(0).astype(np.float64)
+    c = 0.5 * (lo + hi)
+    eye = c + np.array([0.45, -0.35, 0.25])
+    o, d = W.frustum_rays(eye, c, 32, 32, np.random.default_rng(5), fov_y=math.radians(50))
+    Y = np.random.default_rng(6).uniform(0, 1, size=(len(o), 3))
+    params = dict(t_far=1e3, use_clip_box=True, clip_lo=tuple(lo), clip_hi=tuple(hi), T_eps=1e-4)
+    return sc, o.astype(np.float64), d.astype(np.float64), Y, params
+
+
+def fd_crop(sc, o, d, Y, params, n_each=20, seed=3):
+    """Central finite differences of L = 0.5 sum (C - Y)^2 with the FP64
+    oracle for sampled sigma, texel and site parameters (site parameters
+    whose +-h perturbation changes any cell sequence are skipped).
+    Returns list of (kind, index, fd, analytic)."""
+    p = O.make_params(**params)
+    osc = O.OracleScene.from_workload_scene(sc)
+    s64, sig64, tex64 = osc.sites, osc.sigma, osc.tex
+    rgb = O.render(osc, o, d, params=p, n_threads=1)[0]
+    gs, gsig, gt = O.render_bwd(osc, o, d, rgb - Y, params=p)
+    base_cells = O.trace(osc, o, d, params=p, n_threads=1)[0]
+    rng = np.random.default_rng(seed)
+    out = []
+
+    def L(sites=s64, sigma=sig64, tex=tex64):
+        sc2 = O.OracleScene(sites, sigma, tex, sc.offsets, sc.indices)
+        return 0.5 * np.sum((O.render(sc2, o, d, params=p, n_threads=1)[0] - Y) ** 2), sc2
+
+    for i in rng.choice(np.nonzero(np.abs(gsig) > 1e-9)[0], size=n_each, replace=False):
+        h = 1e-6 * max(1.0, sig64[i])
+        v = []
+        for sgn in (1, -1):
+            sg = sig64.copy()
+            sg[i] += sgn * h
+            v.append(L(sigma=sg)[0])
+        out.append(("sigma", (int(i),), (v[0] - v[1]) / (2 * h), gsig[i]))
+    cand = np.argwhere(np.abs(gt) > 1e-9)
+    for q in cand[rng.choice(len(cand), size=n_each, replace=False)]:
+        v = []
+        for sgn in (1, -1):
+            tx = tex64.copy()
+            tx[tuple(q)] += sgn * 1e-3
+            v.append(L(tex=tx)[0])
+        out.append(("tex", tuple(int(x) for x in q), (v[0] - v[1]) / 2e-3, gt[tuple(q)]))
+    cand = np.argwhere(np.abs(gs) > 1e-7)
+    n = 0
+    for q in cand[rng.permutation(len(cand))]:
+        v = []
+        for sgn in (1, -1):
+            ss = s64.copy()
+            ss[q[0], q[1]] += sgn * 1e-7
+            val, sc2 = L(sites=ss)
+            if not np.array_equal(O.trace(sc2, o, d, params=p, n_threads=1)[0], base_cells):
+                v = None
+                break
+            v.append(val)
+        if v is None:
+            continue
+        out.append(("sites", (int(q[0]), int(q[1])), (v[0] - v[1]) / 2e-7, gs[tuple(q)]))
+        n += 1
+        if n >= n_each:
+            break
+    return out, (gs, gsig, gt)
+
+
+def test_fd_on_surface_crop():
+    sc, o, d, Y, params = crop_setup()
+    res, (gs, gsig, gt) = fd_crop(sc, o, d, Y, params)
+    floors = {"sigma": 1e-3 * np.abs(gsig).max(), "tex": 1e-3 * np.abs(gt).max(), "sites": 1e-3 * np.abs(gs).max()}
+    kinds = [r[0] for r in res]
+    assert kinds.count("sites") >= 15 and kinds.count("sigma") == 20 and kinds.count("tex") == 20
+    for kind, idx, fd, an in res:
+        assert abs(fd - an) <= 1e-4 * max(abs(an), floors[kind]), (kind, idx, fd, an)
