@@ -168,13 +168,13 @@ def run_ours(args, ws, rank, local):
     cams = rank_cameras(wl, rank)
     n_img = len(cams)
     c0 = cams[0]
-    spp = c0.lens_samples if c0.kind == 3 else 1
+    spp = c0.spp
     n_rays = sum(c.n_rays for c in cams)
     uniform = all(c.w == c0.w and c.h == c0.h and c.n_rays == c0.n_rays for c in cams)
     if uniform:
         layout = dict(img_w=c0.w * spp, img_h=c0.h, n_images=n_img)
     else:  # one launch over images of different sizes (lens samples widen a row)
-        layout = dict(image_sizes=[(c.w * (c.lens_samples if c.kind == 3 else 1), c.h) for c in cams])
+        layout = dict(image_sizes=[(c.w * c.spp, c.h) for c in cams])
     params = api.make_params(**wl.params, **layout)
     Y = torch.as_tensor(W.target_image(n_rays, wl.seed), device=dev)
 
@@ -268,6 +268,21 @@ def run_ours(args, ws, rank, local):
         m_s, m_f, m_b = timed(scenes[t], max(3, args.steps // 2))
         extra[t] = {"fwd_bwd_mrays_s": round(n_rays / (m_s * 1e-3) / 1e6 * ws, 2), "ms_fwd": round(m_f, 3),
                     "ms_bwd": round(m_b, 3)}
+    if not args.no_extra:
+        # the paper's appearance model (Sec. 5.1-5.2): two maps of logits, sigmoid
+        rng = np.random.default_rng(5000 + wl.seed)
+        tvd = rng.normal(0.0, 0.5, size=wl.scene.tex.shape).astype(np.float32)
+        tvi = rng.normal(0.0, 1.5, size=wl.scene.tex.shape).astype(np.float32)
+        sc_app = api.Scene(wl.scene.sites, wl.scene.sigma, tvi, wl.scene.offsets, wl.scene.indices,
+                           tex_dtype=args.tex, device=dev, tex_vd=tvd)
+        del tvd, tvi
+        params_main = params
+        params = api.make_params(**wl.params, **layout, appearance=1)
+        m_s, m_f, m_b = timed(sc_app, max(3, args.steps // 2))
+        extra["appearance1"] = {"fwd_bwd_mrays_s": round(n_rays / (m_s * 1e-3) / 1e6 * ws, 2),
+                                "ms_fwd": round(m_f, 3), "ms_bwd": round(m_b, 3), "tex": args.tex}
+        params = params_main
+        sc_app.close()
 
     if args.ablation:
         # cumulative: user order + row-major 1-D rays -> + Morton -> + 4x8 tiles -> + skip 1e-3

@@ -76,6 +76,8 @@ typedef struct {
                                   NULL when E == 0                                 */
   int32_t flags;               /* VT_SCENE_KEEP_ORDER: store cells in user order
                                   instead of Morton order (for ablations)         */
+  const float* tex_vd;         /* optional [N,R,R,3] view-dependent texture T_vd
+                                  (Sec. 5.2), logits; required for appearance 1   */
 } vt_scene_desc;
 
 #define VT_SCENE_KEEP_ORDER 1
@@ -100,6 +102,12 @@ typedef struct {
                               the images differ in size (rays laid out image after image,
                               row-major); then img_w/img_h are ignored and n_images <= 64.
                               NULL: img_w/img_h/n_images as above                      */
+  int32_t appearance;      /* 0: colour = tex at the ray direction (default).
+                              1: the paper's model, Sec. 5.1-5.2:
+                              c = sigmoid(T_vi(oct((x - p_i)/|x - p_i|)) + T_vd(oct(-d))),
+                              T_vi = tex, T_vd = tex_vd (logits), x = where the ray
+                              enters the cell (the cell holding the origin: where it
+                              leaves it, or its segment end if it never leaves)      */
 } vt_render_params;
 
 /* Fill `p` with the defaults listed above. */
@@ -117,10 +125,11 @@ void vt_render_params_default(vt_render_params* p);
 vt_status vt_scene_create(const vt_scene_desc* desc, void* stream, vt_scene** out);
 
 /* Replace sites, densities and textures (device pointers, user order, same
- * N, R and adjacency as at creation; any may be NULL to keep the old one).
- * The Morton order of creation is kept. Validates like vt_scene_create. */
+ * N, R and adjacency as at creation; any may be NULL to keep the old one;
+ * tex_vd only if the scene was created with one). The Morton order of
+ * creation is kept. Validates like vt_scene_create. */
 vt_status vt_scene_update(vt_scene* s, const float* sites, const float* sigma, const float* tex,
-                          void* stream);
+                          const float* tex_vd, void* stream);
 
 /* Free a scene. NULL is ignored. Synchronises the device first. */
 void vt_scene_destroy(vt_scene* s);
@@ -148,18 +157,24 @@ vt_status vt_scene_get_error(vt_scene* s, void* stream, int64_t* n_fp64);
  *                     azimuth = atan2(py, px) in the (r, u) plane.
  *   ROLLING_SHUTTER:  pinhole directions; row y has time y/h and origin
  *                     eye + (y/h) * rs_velocity (linear motion per frame).
+ *   MOTION_BLUR:      pinhole directions; lens_samples = S time samples per
+ *                     pixel, sample s at time (s + j)/S with j a SplitMix64
+ *                     counter hash of (seed, pixel, s) as below, origin
+ *                     eye + time * rs_velocity (linear motion over the exposure).
  *   THIN_LENS:        lens_samples = m*m stratified samples per pixel; sample s
  *                     = (sy*m + sx) is jittered in its stratum by a SplitMix64
  *                     counter hash of (seed, pixel, s), mapped to the disk by
  *                     Shirley-Chiu's concentric map, origin eye + lens_radius
  *                     (lx r + ly u); the ray aims at the pinhole ray's point at
  *                     depth focus_dist along f.
- * `time` is 0 except for rolling shutter. */
+ * `time` is 0 except for rolling shutter and motion blur. Average the samples
+ * of a pixel with vt_average_samples. */
 typedef enum {
   VT_CAM_PINHOLE = 0,
   VT_CAM_FISHEYE_EQUIDIST = 1,
   VT_CAM_ROLLING_SHUTTER = 2,
-  VT_CAM_THIN_LENS = 3
+  VT_CAM_THIN_LENS = 3,
+  VT_CAM_MOTION_BLUR = 4
 } vt_cam_kind;
 
 typedef struct {
@@ -168,13 +183,15 @@ typedef struct {
   float eye[3], fwd[3], up[3];
   float fov_y;          /* radians                                   */
   float fisheye_fov;    /* radians across the width (pi = 180 deg)   */
-  float rs_velocity[3]; /* world units per frame                     */
+  float rs_velocity[3]; /* world units per frame (rolling shutter, motion blur) */
   float lens_radius, focus_dist;
-  int32_t lens_samples; /* thin lens: a square number >= 1           */
+  int32_t lens_samples; /* samples per pixel: thin lens (a square number) or
+                           motion blur (>= 1)                        */
   uint64_t seed;
 } vt_camera;
 
-/* Number of rays camera `c` produces (w*h, times lens_samples for thin lens). */
+/* Number of rays camera `c` produces (w*h, times lens_samples for thin lens
+ * and motion blur). */
 int64_t vt_camera_n_rays(const vt_camera* c);
 
 /* Generate rays for n_cams cameras (HOST array of descriptions) into DEVICE
@@ -216,10 +233,11 @@ vt_status vt_render_fwd(vt_scene* s, int64_t n_rays, const float* o, const float
 vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float* d, const float* time,
                         const vt_render_params* p, const float* rgb_out, const float* rgb_residual,
                         const float* grad_rgb, float* grad_sites, float* grad_sigma, float* grad_tex,
-                        void* stream);
+                        float* grad_tex_vd, void* stream);
 
 /* Allocation-free backward (no counterpart in the paper). Same arguments,
- * outputs and numerics as vt_render_bwd without a colour residual, for callers that may not allocate
+ * outputs and numerics as vt_render_bwd without a colour residual, appearance
+ * 0 only (appearance 1 returns VT_ERR_UNSUPPORTED), for callers that may not allocate
  * device memory at the time of the call: vt_render_bwd allocates its gradient
  * scratch with cudaMalloc on its first call for a scene, and cudaMalloc can
  * synchronise the device and bypasses an application's own memory pool or

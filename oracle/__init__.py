@@ -34,12 +34,12 @@ class _Params(C.Structure):
     _fields_ = [("t_near", C.c_double), ("t_far", C.c_double), ("use_clip_box", C.c_int32),
                 ("clip_lo", C.c_double * 3), ("clip_hi", C.c_double * 3), ("T_eps", C.c_double),
                 ("skip_weight", C.c_double), ("bg", C.c_double * 3), ("max_steps", C.c_int32),
-                ("band_eps", C.c_double)]
+                ("band_eps", C.c_double), ("appearance", C.c_int32)]
 
 
 class _Scene(C.Structure):
     _fields_ = [("n", C.c_int64), ("sites", C.c_void_p), ("sigma", C.c_void_p), ("tex", C.c_void_p),
-                ("R", C.c_int32), ("off", C.c_void_p), ("idx", C.c_void_p)]
+                ("R", C.c_int32), ("off", C.c_void_p), ("idx", C.c_void_p), ("tex_vd", C.c_void_p)]
 
 
 class _Camera(C.Structure):
@@ -69,7 +69,11 @@ def lib():
         L.vto_segments.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64] + [C.c_void_p] * 7
         L.vto_segments.restype = C.c_int64
         L.vto_render_bwd.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+        L.vto_render_bwd_dist.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+        L.vto_distortion.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_int]
         L.vto_raygen.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.vto_camera_rays.argtypes = [C.c_void_p]
         L.vto_camera_rays.restype = C.c_int64
@@ -91,9 +95,10 @@ def _ptr(a):
 
 
 class OracleScene:
-    """FP64 copy of a scene (sites, sigma, textures [N,R,R,3], CSR)."""
+    """FP64 copy of a scene (sites, sigma, textures [N,R,R,3], CSR; optional
+    view-dependent logit textures tex_vd for appearance mode 1)."""
 
-    def __init__(self, sites, sigma, tex, offsets, indices):
+    def __init__(self, sites, sigma, tex, offsets, indices, tex_vd=None):
         self.sites = _f64(sites).reshape(-1, 3)
         self.sigma = _f64(sigma).reshape(-1)
         self.tex = _f64(tex)
@@ -101,8 +106,9 @@ class OracleScene:
         self.off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
         self.idx = np.ascontiguousarray(np.asarray(indices, dtype=np.int32))
         self.n = len(self.sites)
+        self.tex_vd = None if tex_vd is None else _f64(tex_vd)
         self._s = _Scene(self.n, _ptr(self.sites), _ptr(self.sigma), _ptr(self.tex), self.R, _ptr(self.off),
-                         _ptr(self.idx))
+                         _ptr(self.idx), _ptr(self.tex_vd))
 
     @classmethod
     def from_workload_scene(cls, sc):
@@ -110,9 +116,9 @@ class OracleScene:
 
 
 def make_params(t_near=0.0, t_far=20.0, use_clip_box=False, clip_lo=(0, 0, 0), clip_hi=(1, 1, 1), T_eps=1e-4,
-                skip_weight=0.0, bg=(1, 1, 1), max_steps=1 << 20, band_eps=1e-6):
+                skip_weight=0.0, bg=(1, 1, 1), max_steps=1 << 20, band_eps=1e-6, appearance=0):
     return _Params(t_near, t_far, int(bool(use_clip_box)), (C.c_double * 3)(*clip_lo), (C.c_double * 3)(*clip_hi),
-                   T_eps, skip_weight, (C.c_double * 3)(*bg), max_steps, band_eps)
+                   T_eps, skip_weight, (C.c_double * 3)(*bg), max_steps, band_eps, int(appearance))
 
 
 def _threads(n):
@@ -166,18 +172,43 @@ def segments(sc: OracleScene, o, d, cap=4096, params=None, **kw):
     return {k: v[:m] for k, v in out.items()}
 
 
-def render_bwd(sc: OracleScene, o, d, grad_rgb, params=None, n_threads=0, **kw):
-    """FP64 gradients (sites [N,3], sigma [N], tex [N,R,R,3]) for dL/dC."""
+def render_bwd(sc: OracleScene, o, d, grad_rgb, params=None, n_threads=0, grad_dist=None, **kw):
+    """FP64 gradients (sites [N,3], sigma [N], tex [N,R,R,3]) for dL/dC and,
+    if grad_dist [R] is given, dL/dL_dist per ray (distortion loss, Eq. 2);
+    a fourth array (tex_vd gradient) is returned when the scene has tex_vd."""
     p = params if params is not None else make_params(**kw)
     o, d, g = _f64(o).reshape(-1, 3), _f64(d).reshape(-1, 3), _f64(grad_rgb).reshape(-1, 3)
+    gd = None if grad_dist is None else _f64(grad_dist).reshape(-1)
     gs = np.zeros((sc.n, 3))
     gsig = np.zeros(sc.n)
     gt = np.zeros(sc.tex.shape)
-    st = lib().vto_render_bwd(C.byref(sc._s), len(o), _ptr(o), _ptr(d), C.byref(p), _ptr(g), _ptr(gs), _ptr(gsig),
-                              _ptr(gt), _threads(n_threads))
+    gtv = None if sc.tex_vd is None else np.zeros(sc.tex.shape)
+    st = lib().vto_render_bwd_dist(C.byref(sc._s), len(o), _ptr(o), _ptr(d), C.byref(p), _ptr(g), _ptr(gd), _ptr(gs),
+                                   _ptr(gsig), _ptr(gt), _ptr(gtv), _threads(n_threads))
     if st:
         raise RuntimeError(f"oracle bwd failed: {st}")
-    return gs, gsig, gt
+    return (gs, gsig, gt) if gtv is None else (gs, gsig, gt, gtv)
+
+
+def distortion(sc: OracleScene, o, d, params=None, n_threads=0, **kw):
+    """Per-ray distortion loss L_dist [R] (Eq. 2) over the composited intervals."""
+    p = params if params is not None else make_params(**kw)
+    o, d = _f64(o).reshape(-1, 3), _f64(d).reshape(-1, 3)
+    L = np.zeros(len(o))
+    st = lib().vto_distortion(C.byref(sc._s), len(o), _ptr(o), _ptr(d), C.byref(p), _ptr(L), _threads(n_threads))
+    if st:
+        raise RuntimeError(f"oracle distortion failed: {st}")
+    return L
+
+
+def density_from_log(rho):
+    """sigma = exp(rho) (Sec. 5.4, scale-invariant density)."""
+    return np.exp(_f64(rho))
+
+
+def density_log_bwd(sigma, grad_sigma):
+    """dL/drho = dL/dsigma * sigma (Eq. 4)."""
+    return _f64(grad_sigma) * _f64(sigma)
 
 
 def octahedral(d):

@@ -21,12 +21,21 @@
  *       C = sum_k T_k alpha_k c_k + T_final * bg,
  *     stopping after the cell at which T < T_eps (early termination, Sec. 3.2).
  *   - Colour = bilinear fetch of the cell's R x R octahedral texture at the
- *     ray direction (Sec. 5.1 octahedral map, read "at the ray direction").
+ *     ray direction (Sec. 5.1 octahedral map, read "at the ray direction");
+ *     or, in appearance mode 1, the paper's model (Sec. 5.1-5.2):
+ *       c = sigmoid(T_vi(oct((x - p_i)/|x - p_i|)) + T_vd(oct(omega))),
+ *     x = the point where the ray enters the cell (for the cell holding the
+ *     origin: where it leaves it, or the end of its segment if it never
+ *     leaves), omega = -d/|d| (towards the ray origin).
  *   - Backward: analytic adjoint of the above from the stored segment list
  *     (density gradient consistent with Eq. 3; plane-crossing gradient by
  *     differentiating t_j with respect to both sites).
- *   - Ray generation for pinhole, equidistant fisheye, rolling-shutter and
- *     thin-lens cameras (Sec. 6.5 and the application appendix).
+ *   - Distortion loss of Mip-NeRF 360 (Eq. 2) per ray, over the composited
+ *     intervals [a_k, b_k] with weights w_k = T_k alpha_k and s(t) = 1 - 1/(1+t):
+ *       L = sum_{k,l} w_k w_l |sbar_k - sbar_l| + 1/3 sum_k w_k^2 ds_k,
+ *     written out as the double sum; its gradient from the same definition.
+ *   - Ray generation for pinhole, equidistant fisheye, rolling-shutter,
+ *     thin-lens and motion-blur cameras (Sec. 6.5 and the application appendix).
  *
  * Readings where the paper is silent (each listed in the design notes):
  *   sign(0) = +1 in the lower-hemisphere unfold; texel coordinates clamp to
@@ -67,6 +76,7 @@ typedef struct {
   double bg[3];
   int32_t max_steps;
   double band_eps;
+  int32_t appearance; /* 0: one texture at the ray direction; 1: Sec. 5.1-5.2 model */
 } vto_params;
 
 typedef struct {
@@ -77,6 +87,7 @@ typedef struct {
   int32_t R;
   const int64_t* off; /* [n+1]        */
   const int32_t* idx; /* [E]          */
+  const double* tex_vd; /* [n,R,R,3] view-dependent logits (appearance 1) */
 } vto_scene;
 
 /* ------------------------------------------------------------------ */
@@ -132,6 +143,28 @@ static void cell_colour(const vto_scene* sc, int64_t cell, const int64_t taps[4]
     for (int ch = 0; ch < 3; ++ch) c[ch] += tw[q] * t[taps[q] * 3 + ch];
 }
 
+/* Appearance 1 (Sec. 5.1-5.2): logit z = T_vi(oct(dsurf)) + T_vd(oct(-d)),
+ * c = sigmoid(z). */
+static void cell_colour_paper(const vto_scene* sc, int64_t cell, const double dsurf[3], const double d[3],
+                              double c[3]) {
+  int64_t RR = (int64_t)sc->R * sc->R;
+  double uv[2], w[4];
+  int64_t tp[4];
+  double z[3] = {0.0, 0.0, 0.0};
+  vto_oct(dsurf, uv);
+  vto_bilinear_taps(sc->R, uv[0], uv[1], tp, w);
+  const double* t = sc->tex + cell * RR * 3;
+  for (int q = 0; q < 4; ++q)
+    for (int ch = 0; ch < 3; ++ch) z[ch] += w[q] * t[tp[q] * 3 + ch];
+  double om[3] = {-d[0], -d[1], -d[2]};
+  vto_oct(om, uv);
+  vto_bilinear_taps(sc->R, uv[0], uv[1], tp, w);
+  const double* tv = sc->tex_vd + cell * RR * 3;
+  for (int q = 0; q < 4; ++q)
+    for (int ch = 0; ch < 3; ++ch) z[ch] += w[q] * tv[tp[q] * 3 + ch];
+  for (int ch = 0; ch < 3; ++ch) c[ch] = 1.0 / (1.0 + exp(-z[ch]));
+}
+
 /* Brute-force nearest site (Sec. 3.1 cell definition); ties -> lowest id. */
 int64_t vto_nearest(int64_t n, const double* sites, const double q[3]) {
   int64_t best = -1;
@@ -166,6 +199,10 @@ typedef struct {
   int32_t composited, coloured;
   double delta, alpha, T_before, w;
   double c[3];
+  /* appearance 1: surface point x = o + t_x d, which crossing it lies on
+   * (0: entry face, 1: exit face, -1: none), direction from the site */
+  double t_x, dsurf[3], rlen;
+  int32_t x_on;
 } vto_seg;
 
 typedef struct {
@@ -304,7 +341,25 @@ static int walk_ray(const vto_scene* sc, const vto_params* p, const double o[3],
       if (p->skip_weight > 0.0 && fabs(w / p->skip_weight - 1.0) < 1e-4) *flags |= VTO_F_SKIP_AMBIG;
       if (!(p->skip_weight > 0.0) || w >= p->skip_weight) {
         s.coloured = 1;
-        cell_colour(sc, cell, taps, tw, s.c);
+        if (p->appearance == 1) {
+          /* surface point: entry face, else (origin cell) exit face, else segment end */
+          if (k > 1) {
+            s.t_x = t_in;
+            s.x_on = 0;
+          } else if (isfinite(best_t)) {
+            s.t_x = best_t;
+            s.x_on = 1;
+          } else {
+            s.t_x = t1;
+            s.x_on = -1;
+          }
+          double v[3] = {o[0] + s.t_x * d[0] - si[0], o[1] + s.t_x * d[1] - si[1], o[2] + s.t_x * d[2] - si[2]};
+          s.rlen = sqrt(dot3(v, v));
+          for (int c3 = 0; c3 < 3; ++c3) s.dsurf[c3] = s.rlen > 0.0 ? v[c3] / s.rlen : d[c3] / dn;
+          cell_colour_paper(sc, cell, s.dsurf, d, s.c);
+        } else {
+          cell_colour(sc, cell, taps, tw, s.c);
+        }
         for (int ch = 0; ch < 3; ++ch) C[ch] += w * s.c[ch];
       }
       T = T * e;
@@ -465,6 +520,107 @@ int64_t vto_segments(const vto_scene* sc, const double o[3], const double d[3], 
   return n;
 }
 
+/* Bilinear value and its derivatives with respect to (u, v) for one cell's
+ * texture (zero derivative where the texel coordinate is clamped). */
+static void bilinear_uv_grad(int32_t R, const double* t, double u, double v, double dzdu[3], double dzdv[3]) {
+  double x = (u + 1.0) * 0.5 * R - 0.5, y = (v + 1.0) * 0.5 * R - 0.5;
+  double cx = (x >= 0.0 && x <= R - 1.0) ? 0.5 * R : 0.0;
+  double cy = (y >= 0.0 && y <= R - 1.0) ? 0.5 * R : 0.0;
+  if (x < 0.0) x = 0.0;
+  if (x > R - 1.0) x = R - 1.0;
+  if (y < 0.0) y = 0.0;
+  if (y > R - 1.0) y = R - 1.0;
+  int64_t x0 = (int64_t)floor(x), y0 = (int64_t)floor(y);
+  if (x0 > R - 1) x0 = R - 1;
+  if (y0 > R - 1) y0 = R - 1;
+  int64_t x1 = x0 + 1 < R ? x0 + 1 : R - 1, y1 = y0 + 1 < R ? y0 + 1 : R - 1;
+  double fx = x - (double)x0, fy = y - (double)y0;
+  for (int c = 0; c < 3; ++c) {
+    double t00 = t[(y0 * R + x0) * 3 + c], t01 = t[(y0 * R + x1) * 3 + c];
+    double t10 = t[(y1 * R + x0) * 3 + c], t11 = t[(y1 * R + x1) * 3 + c];
+    dzdu[c] = cx * ((1.0 - fy) * (t01 - t00) + fy * (t11 - t10));
+    dzdv[c] = cy * ((1.0 - fx) * (t10 - t00) + fx * (t11 - t01));
+  }
+}
+
+/* g_d = (d(u,v)/dd)^T (gu, gv) for the octahedral map of direction d. */
+static void oct_vjp(const double d[3], double gu, double gv, double gd[3]) {
+  double l1 = fabs(d[0]) + fabs(d[1]) + fabs(d[2]);
+  double q[3] = {d[0] / l1, d[1] / l1, d[2] / l1};
+  double sg[3] = {d[0] >= 0.0 ? 1.0 : -1.0, d[1] >= 0.0 ? 1.0 : -1.0, d[2] >= 0.0 ? 1.0 : -1.0};
+  for (int j = 0; j < 3; ++j) {
+    double dq0 = ((j == 0) - q[0] * sg[j]) / l1, dq1 = ((j == 1) - q[1] * sg[j]) / l1;
+    double du, dv;
+    if (d[2] >= 0.0) {
+      du = dq0;
+      dv = dq1;
+    } else {
+      du = -sg[0] * sg[1] * dq1;
+      dv = -sg[1] * sg[0] * dq0;
+    }
+    gd[j] = gu * du + gv * dv;
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Distortion loss (Eq. 2) from the plain definition.                    */
+static double s_of_t(double t) { return 1.0 - 1.0 / (1.0 + t); }
+
+static double ray_distortion(const seg_buf* sb) {
+  double L = 0.0;
+  for (int64_t k = 0; k < sb->n; ++k) {
+    const vto_seg* a = &sb->s[k];
+    if (!a->composited) continue;
+    double sk = 0.5 * (s_of_t(a->a) + s_of_t(a->b));
+    for (int64_t l = 0; l < sb->n; ++l) {
+      const vto_seg* b = &sb->s[l];
+      if (!b->composited) continue;
+      double sl = 0.5 * (s_of_t(b->a) + s_of_t(b->b));
+      L += a->w * b->w * fabs(sk - sl);
+    }
+    L += a->w * a->w * (s_of_t(a->b) - s_of_t(a->a)) / 3.0;
+  }
+  return L;
+}
+
+/* Adds gd * dL_dist/dtau_k to dtau[] and the direct derivatives of L_dist
+ * with respect to the interval ends to the crossing terms xterm[] (index q:
+ * the crossing at the exit of walked cell q):
+ *   dL/dw_k    = 2 sum_l w_l |sbar_k - sbar_l| + 2/3 w_k ds_k
+ *   dL/dsbar_k = 2 w_k sum_l w_l sign(sbar_k - sbar_l)
+ *   dL/dds_k   = w_k^2 / 3
+ *   w_k = T_k alpha_k: dw_k/dtau_j = -w_k (j < k), T_{k+1} (j = k)
+ *   sbar = (s(a)+s(b))/2, ds = s(b)-s(a), s'(t) = 1/(1+t)^2.
+ * An interval end moves with a crossing only where it is one (b_k = exit
+ * crossing below t_far', a_k = entry crossing above t_near').            */
+static void ray_distortion_bwd(const seg_buf* sb, double gd, double t0, double t1, double* dtau, double* xterm) {
+  for (int64_t k = 0; k < sb->n; ++k) {
+    const vto_seg* a = &sb->s[k];
+    if (!a->composited) continue;
+    double sk = 0.5 * (s_of_t(a->a) + s_of_t(a->b));
+    double dw = 0.0, dsbar = 0.0;
+    for (int64_t l = 0; l < sb->n; ++l) {
+      const vto_seg* b = &sb->s[l];
+      if (!b->composited) continue;
+      double sl = 0.5 * (s_of_t(b->a) + s_of_t(b->b));
+      dw += 2.0 * b->w * fabs(sk - sl);
+      if (l != k) dsbar += 2.0 * a->w * b->w * (sk > sl ? 1.0 : (sk < sl ? -1.0 : 0.0));
+    }
+    double dsk = s_of_t(a->b) - s_of_t(a->a);
+    dw += 2.0 / 3.0 * a->w * dsk;
+    double dds = a->w * a->w / 3.0;
+    /* through the weights */
+    dtau[k] += gd * dw * a->T_before * (1.0 - a->alpha);
+    for (int64_t j = 0; j < k; ++j)
+      if (sb->s[j].composited) dtau[j] -= gd * dw * a->w;
+    /* through the interval ends */
+    double sa = 1.0 / ((1.0 + a->a) * (1.0 + a->a)), sbb = 1.0 / ((1.0 + a->b) * (1.0 + a->b));
+    double dLda = gd * sa * (0.5 * dsbar - dds), dLdb = gd * sbb * (0.5 * dsbar + dds);
+    if (a->b == a->t_out && a->t_out < t1) xterm[k] += dLdb;
+    if (k > 0 && a->a == a->t_in && a->t_in > t0) xterm[k - 1] += dLda;
+  }
+}
+
 /* Gradient contributions are produced per thread as (flat index, value)
  * pairs -- flat index: [0,3N) sites, [3N,4N) sigma, then texels -- and added
  * into the outputs under a mutex. */
@@ -482,7 +638,8 @@ typedef struct {
   const vto_scene* sc;
   const vto_params* p;
   const double *o, *d, *g;
-  double *g_sites, *g_sigma, *g_tex;
+  const double* gdist; /* dL/dL_dist per ray, or NULL */
+  double *g_sites, *g_sigma, *g_tex, *g_tex_vd;
   int64_t lo, hi;
   pthread_mutex_t* mu;
   int status;
@@ -505,6 +662,7 @@ static int emit(contrib_buf* b, int64_t i, double v) {
 
 static void flush_contribs(bwd_job* J, contrib_buf* b) {
   int64_t n3 = 3 * J->sc->n, n4 = 4 * J->sc->n;
+  int64_t nt = n4 + J->sc->n * (int64_t)J->sc->R * J->sc->R * 3;
   pthread_mutex_lock(J->mu);
   for (int64_t k = 0; k < b->n; ++k) {
     int64_t i = b->c[k].i;
@@ -512,8 +670,10 @@ static void flush_contribs(bwd_job* J, contrib_buf* b) {
       J->g_sites[i] += b->c[k].v;
     else if (i < n4)
       J->g_sigma[i - n3] += b->c[k].v;
-    else
+    else if (i < nt)
       J->g_tex[i - n4] += b->c[k].v;
+    else if (J->g_tex_vd)
+      J->g_tex_vd[i - nt] += b->c[k].v;
   }
   pthread_mutex_unlock(J->mu);
   b->n = 0;
@@ -526,6 +686,7 @@ static void* bwd_worker(void* arg) {
   seg_buf sb = {0, 0, 0};
   contrib_buf cb = {0, 0, 0};
   double* dtau = NULL;
+  double* xterm = NULL;
   int64_t dcap = 0;
   const int64_t RR = (int64_t)sc->R * sc->R, n3 = 3 * sc->n, n4 = 4 * sc->n;
   J->status = VTO_OK;
@@ -548,11 +709,13 @@ static void* bwd_worker(void* arg) {
     if (sb.n > dcap) {
       dcap = sb.n * 2;
       double* nd = (double*)realloc(dtau, (size_t)dcap * sizeof(double));
-      if (!nd) {
+      double* nx = (double*)realloc(xterm, (size_t)dcap * sizeof(double));
+      if (nd) dtau = nd;
+      if (nx) xterm = nx;
+      if (!nd || !nx) {
         J->status = VTO_ERR_MEM;
         break;
       }
-      dtau = nd;
     }
     double uv[2];
     vto_oct(drr, uv);
@@ -573,21 +736,67 @@ static void* bwd_worker(void* arg) {
         for (int ch = 0; ch < 3; ++ch) S[ch] += s->w * s->c[ch];
     }
     int st = VTO_OK;
+    const int64_t ntex = n4 + sc->n * RR * 3;
+    /* direct dL/dt terms of crossings: appearance 1 colour and the distortion loss */
+    for (int64_t q = 0; q < sb.n; ++q) xterm[q] = 0.0;
+    if (J->gdist && J->gdist[r] != 0.0) ray_distortion_bwd(&sb, J->gdist[r], t0, t1, dtau, xterm);
     for (int64_t q = 0; q < sb.n && st == VTO_OK; ++q) {
       vto_seg* s = &sb.s[q];
       int64_t i = s->cell;
       if (s->composited) {
         st |= emit(&cb, n3 + i, dtau[q] * s->delta);
-        if (s->coloured)
+        if (s->coloured && p->appearance == 1) {
+          /* c = sigmoid(z): dL/dz = g w c (1 - c) */
+          double gz[3];
+          for (int ch = 0; ch < 3; ++ch) gz[ch] = g[ch] * s->w * s->c[ch] * (1.0 - s->c[ch]);
+          double uv[2], tw2[4];
+          int64_t tp2[4];
+          vto_oct(s->dsurf, uv);
+          vto_bilinear_taps(sc->R, uv[0], uv[1], tp2, tw2);
+          for (int tq = 0; tq < 4; ++tq)
+            for (int ch = 0; ch < 3; ++ch) st |= emit(&cb, n4 + (i * RR + tp2[tq]) * 3 + ch, gz[ch] * tw2[tq]);
+          double om[3] = {-drr[0], -drr[1], -drr[2]}, uvv[2];
+          vto_oct(om, uvv);
+          vto_bilinear_taps(sc->R, uvv[0], uvv[1], tp2, tw2);
+          for (int tq = 0; tq < 4; ++tq)
+            for (int ch = 0; ch < 3; ++ch) st |= emit(&cb, ntex + (i * RR + tp2[tq]) * 3 + ch, gz[ch] * tw2[tq]);
+          /* through the surface direction: dsurf = (x - p)/|x - p|, x = o + t_x d */
+          double dzdu[3], dzdv[3];
+          bilinear_uv_grad(sc->R, sc->tex + i * RR * 3, uv[0], uv[1], dzdu, dzdv);
+          double gu = 0.0, gv = 0.0;
+          for (int ch = 0; ch < 3; ++ch) {
+            gu += gz[ch] * dzdu[ch];
+            gv += gz[ch] * dzdv[ch];
+          }
+          double gd[3];
+          oct_vjp(s->dsurf, gu, gv, gd);
+          if (s->rlen > 0.0) {
+            double dd = dot3(gd, s->dsurf);
+            double gx[3];
+            for (int c3 = 0; c3 < 3; ++c3) gx[c3] = (gd[c3] - s->dsurf[c3] * dd) / s->rlen;
+            for (int c3 = 0; c3 < 3; ++c3) st |= emit(&cb, 3 * i + c3, -gx[c3]);
+            double gt = dot3(gx, drr);
+            if (s->x_on == 0 && q > 0) xterm[q - 1] += gt;
+            if (s->x_on == 1) xterm[q] += gt;
+          }
+        } else if (s->coloured) {
           for (int tq = 0; tq < 4; ++tq)
             for (int ch = 0; ch < 3; ++ch) st |= emit(&cb, n4 + (i * RR + taps[tq]) * 3 + ch, g[ch] * s->w * tw[tq]);
+        }
       }
+    }
+    for (int64_t q = 0; q < sb.n && st == VTO_OK; ++q) {
+      vto_seg* s = &sb.s[q];
+      int64_t i = s->cell;
       /* crossing at the exit of this cell */
       int64_t j = s->next;
       double tb = s->t_out;
-      if (j < 0 || !(tb > t0) || !(tb < t1)) continue;
-      double dt_b = sc->sigma[i] * dtau[q];
-      if (q + 1 < sb.n) dt_b -= sc->sigma[j] * dtau[q + 1];
+      if (j < 0 || !isfinite(tb)) continue;
+      double dt_b = xterm[q];
+      if (tb > t0 && tb < t1) {
+        dt_b += sc->sigma[i] * dtau[q];
+        if (q + 1 < sb.n) dt_b -= sc->sigma[j] * dtau[q + 1];
+      }
       if (dt_b == 0.0) continue;
       const double* si = sc->sites + 3 * i;
       const double* sj = sc->sites + 3 * j;
@@ -606,6 +815,7 @@ static void* bwd_worker(void* arg) {
   free(cb.c);
   free(sb.s);
   free(dtau);
+  free(xterm);
   return NULL;
 }
 
@@ -623,9 +833,9 @@ static void* bwd_worker(void* arg) {
  *     dt_b/ds_{k+1} = (s_{k+1} - x_b) / (n.d),  n = s_{k+1} - s_k.
  * When the walk stopped by transmittance inside (t_near', t_far'), the exit
  * plane of the last cell still moves delta_K; its far side gets no dtau. */
-int vto_render_bwd(const vto_scene* sc, int64_t n_rays, const double* o, const double* d,
-                   const vto_params* p, const double* grad_rgb, double* g_sites, double* g_sigma,
-                   double* g_tex, int n_threads) {
+int vto_render_bwd_dist(const vto_scene* sc, int64_t n_rays, const double* o, const double* d,
+                        const vto_params* p, const double* grad_rgb, const double* grad_dist, double* g_sites,
+                        double* g_sigma, double* g_tex, double* g_tex_vd, int n_threads) {
   if (n_threads < 1) n_threads = 1;
   if (n_threads > 256) n_threads = 256;
   if (n_rays < n_threads) n_threads = n_rays > 0 ? (int)n_rays : 1;
@@ -640,9 +850,11 @@ int vto_render_bwd(const vto_scene* sc, int64_t n_rays, const double* o, const d
     jobs[t].o = o;
     jobs[t].d = d;
     jobs[t].g = grad_rgb;
+    jobs[t].gdist = grad_dist;
     jobs[t].g_sites = g_sites;
     jobs[t].g_sigma = g_sigma;
     jobs[t].g_tex = g_tex;
+    jobs[t].g_tex_vd = g_tex_vd;
     jobs[t].mu = &mu;
     jobs[t].lo = t * chunk;
     jobs[t].hi = (t + 1) * chunk < n_rays ? (t + 1) * chunk : n_rays;
@@ -663,20 +875,86 @@ int vto_render_bwd(const vto_scene* sc, int64_t n_rays, const double* o, const d
   return st;
 }
 
+int vto_render_bwd(const vto_scene* sc, int64_t n_rays, const double* o, const double* d,
+                   const vto_params* p, const double* grad_rgb, double* g_sites, double* g_sigma,
+                   double* g_tex, double* g_tex_vd, int n_threads) {
+  return vto_render_bwd_dist(sc, n_rays, o, d, p, grad_rgb, NULL, g_sites, g_sigma, g_tex, g_tex_vd, n_threads);
+}
+
+/* Per-ray distortion loss L_dist (Eq. 2). */
+typedef struct {
+  const vto_scene* sc;
+  const vto_params* p;
+  const double *o, *d;
+  double* L;
+  int64_t lo, hi;
+  int status;
+} dist_job;
+
+static void* dist_worker(void* arg) {
+  dist_job* J = (dist_job*)arg;
+  seg_buf b = {0, 0, 0};
+  J->status = VTO_OK;
+  for (int64_t r = J->lo; r < J->hi; ++r) {
+    double C[3], T, lt;
+    int32_t k, fl;
+    int64_t ln;
+    if (walk_ray(J->sc, J->p, J->o + 3 * r, J->d + 3 * r, &b, C, &T, &k, &fl, &ln, &lt) != VTO_OK) {
+      J->status = VTO_ERR_MEM;
+      break;
+    }
+    J->L[r] = ray_distortion(&b);
+  }
+  free(b.s);
+  return NULL;
+}
+
+int vto_distortion(const vto_scene* sc, int64_t n_rays, const double* o, const double* d, const vto_params* p,
+                   double* L, int n_threads) {
+  if (n_threads < 1) n_threads = 1;
+  if (n_threads > 256) n_threads = 256;
+  if (n_rays < n_threads) n_threads = n_rays > 0 ? (int)n_rays : 1;
+  pthread_t th[256];
+  dist_job jobs[256];
+  int64_t chunk = (n_rays + n_threads - 1) / n_threads;
+  for (int t = 0; t < n_threads; ++t) {
+    jobs[t].sc = sc;
+    jobs[t].p = p;
+    jobs[t].o = o;
+    jobs[t].d = d;
+    jobs[t].L = L;
+    jobs[t].lo = t * chunk;
+    jobs[t].hi = (t + 1) * chunk < n_rays ? (t + 1) * chunk : n_rays;
+    jobs[t].status = VTO_OK;
+    if (jobs[t].lo >= jobs[t].hi) continue;
+    if (n_threads == 1)
+      dist_worker(&jobs[t]);
+    else
+      pthread_create(&th[t], NULL, dist_worker, &jobs[t]);
+  }
+  int st = VTO_OK;
+  for (int t = 0; t < n_threads; ++t) {
+    if (jobs[t].lo >= jobs[t].hi) continue;
+    if (n_threads > 1) pthread_join(th[t], NULL);
+    if (jobs[t].status != VTO_OK) st = jobs[t].status;
+  }
+  return st;
+}
+
 /* ------------------------------------------------------------------ */
 /* Ray generation (Sec. 6.5: only the rays change between camera models).
  * Basis: f = fwd/|fwd|, r = (f x up)/|f x up|, u = r x f. Pixel (x, y) with
  * row 0 at the top, sample point at the pixel centre. Ray order:
  * [row][col][lens sample]. Directions are unit length.                      */
 typedef struct {
-  int32_t kind; /* 0 pinhole, 1 equidistant fisheye, 2 rolling shutter, 3 thin lens */
+  int32_t kind; /* 0 pinhole, 1 equidistant fisheye, 2 rolling shutter, 3 thin lens, 4 motion blur */
   int32_t w, h;
   double eye[3], fwd[3], up[3];
   double fov_y;         /* pinhole-type vertical field of view (radians)   */
   double fisheye_fov;   /* fisheye field of view across the width (rad)     */
-  double rs_velocity[3];/* rolling shutter: centre moves velocity*time       */
+  double rs_velocity[3];/* rolling shutter / motion blur: centre moves velocity*time */
   double lens_radius, focus_dist;
-  int32_t lens_samples; /* thin lens: square number of stratified samples    */
+  int32_t lens_samples; /* samples per pixel: thin lens (a square number) or motion blur */
   uint64_t seed;
 } vto_camera;
 
@@ -724,7 +1002,7 @@ void vto_concentric(double a, double b, double out[2]) {
 }
 
 int64_t vto_camera_rays(const vto_camera* c) {
-  int64_t s = c->kind == 3 ? c->lens_samples : 1;
+  int64_t s = (c->kind == 3 || c->kind == 4) ? c->lens_samples : 1;
   return (int64_t)c->w * c->h * s;
 }
 
@@ -741,6 +1019,9 @@ int vto_raygen(const vto_camera* c, double* o, double* d, double* time) {
     S = c->lens_samples;
     m = (int32_t)floor(sqrt((double)S) + 0.5);
     if (S <= 0 || m * m != S) return VTO_ERR_ARG;
+  } else if (c->kind == 4) {
+    S = c->lens_samples;
+    if (S <= 0) return VTO_ERR_ARG;
   }
   double ty = tan(0.5 * c->fov_y), tx = ty * (double)c->w / (double)c->h;
   double fpx = (0.5 * c->w) / (0.5 * c->fisheye_fov);
@@ -779,6 +1060,13 @@ int vto_raygen(const vto_camera* c, double* o, double* d, double* time) {
               oo[k] += c->lens_radius * (disk[0] * r[k] + disk[1] * u[k]);
             /* point on the plane of focus (pd.f == 1, so depth focus_dist) */
             for (int k = 0; k < 3; ++k) dd[k] = c->eye[k] + c->focus_dist * pd[k] - oo[k];
+          } else if (c->kind == 4) {
+            /* motion blur (Sec. 6.5): S stratified, jittered times over the
+             * exposure [0,1), camera centre moved linearly */
+            uint64_t pix = (uint64_t)y * c->w + x;
+            tm = (s + vto_uniform(c->seed, (pix * S + s) << 1)) / S;
+            for (int k = 0; k < 3; ++k) oo[k] += tm * c->rs_velocity[k];
+            for (int k = 0; k < 3; ++k) dd[k] = pd[k];
           } else {
             for (int k = 0; k < 3; ++k) dd[k] = pd[k];
           }

@@ -16,7 +16,7 @@ LIB_PATH = os.environ.get("VT_LIB_PATH") or os.path.join(HERE, "libvt.so")
 
 VT_OK, VT_ERR_INVALID_ARG, VT_ERR_CUDA, VT_ERR_OOM, VT_ERR_MAX_STEPS, VT_ERR_CAPACITY, VT_ERR_UNSUPPORTED = range(7)
 VT_F32, VT_F16, VT_BF16 = 0, 1, 2
-VT_CAM_PINHOLE, VT_CAM_FISHEYE_EQUIDIST, VT_CAM_ROLLING_SHUTTER, VT_CAM_THIN_LENS = 0, 1, 2, 3
+VT_CAM_PINHOLE, VT_CAM_FISHEYE_EQUIDIST, VT_CAM_ROLLING_SHUTTER, VT_CAM_THIN_LENS, VT_CAM_MOTION_BLUR = 0, 1, 2, 3, 4
 
 # every symbol include/vt.h declares
 EXPORTS = ["vt_render_params_default", "vt_scene_create", "vt_scene_update", "vt_scene_destroy", "vt_scene_info",
@@ -33,7 +33,7 @@ class VTError(RuntimeError):
 class vt_scene_desc(C.Structure):
     _fields_ = [("n_sites", C.c_int64), ("tex_res", C.c_int32), ("tex_dtype", C.c_int32), ("sites", C.c_void_p),
                 ("sigma", C.c_void_p), ("tex", C.c_void_p), ("adj_offsets", C.c_void_p),
-                ("adj_indices", C.c_void_p), ("flags", C.c_int32)]
+                ("adj_indices", C.c_void_p), ("flags", C.c_int32), ("tex_vd", C.c_void_p)]
 
 
 VT_SCENE_KEEP_ORDER = 1
@@ -43,7 +43,8 @@ class vt_render_params(C.Structure):
     _fields_ = [("t_near", C.c_float), ("t_far", C.c_float), ("use_clip_box", C.c_int32),
                 ("clip_lo", C.c_float * 3), ("clip_hi", C.c_float * 3), ("T_eps", C.c_float),
                 ("skip_weight", C.c_float), ("bg", C.c_float * 3), ("img_w", C.c_int32), ("img_h", C.c_int32),
-                ("n_images", C.c_int32), ("max_steps", C.c_int32), ("image_sizes", C.c_void_p)]
+                ("n_images", C.c_int32), ("max_steps", C.c_int32), ("image_sizes", C.c_void_p),
+                ("appearance", C.c_int32)]
 
 
 class vt_camera(C.Structure):
@@ -62,14 +63,14 @@ def _load():
     sig = {
         "vt_render_params_default": ([P], None),
         "vt_scene_create": ([P, P, P], C.c_int),
-        "vt_scene_update": ([P, P, P, P, P], C.c_int),
+        "vt_scene_update": ([P, P, P, P, P, P], C.c_int),
         "vt_scene_destroy": ([P], None),
         "vt_scene_info": ([P, P, P, P, P], C.c_int),
         "vt_scene_get_error": ([P, P, P], C.c_int),
         "vt_camera_n_rays": ([P], I64),
         "vt_generate_rays": ([P, I32, P, P, P, P], C.c_int),
         "vt_render_fwd": ([P, I64, P, P, P, P, P, P, P, P, P], C.c_int),
-        "vt_render_bwd": ([P, I64, P, P, P, P, P, P, P, P, P, P, P], C.c_int),
+        "vt_render_bwd": ([P, I64, P, P, P, P, P, P, P, P, P, P, P, P], C.c_int),
         "vt_render_bwd_static": ([P, I64, P, P, P, P, P, P, P, P, P, P], C.c_int),
         "vt_trace_cells": ([P, I64, P, P, P, I32, P, P, P, P], C.c_int),
         "vt_l2_loss": ([I64, P, P, P, P, P], C.c_int),
@@ -110,9 +111,9 @@ def vt_scene_create(desc: vt_scene_desc, stream: int) -> int:
     return h.value
 
 
-def vt_scene_update(scene: int, sites: int, sigma: int, tex: int, stream: int):
+def vt_scene_update(scene: int, sites: int, sigma: int, tex: int, tex_vd: int, stream: int):
     check(lib.vt_scene_update(C.c_void_p(scene), C.c_void_p(sites), C.c_void_p(sigma), C.c_void_p(tex),
-                              C.c_void_p(stream)), "vt_scene_update")
+                              C.c_void_p(tex_vd), C.c_void_p(stream)), "vt_scene_update")
 
 
 def vt_scene_destroy(scene: int):
@@ -150,11 +151,12 @@ def vt_render_fwd(scene: int, n_rays: int, o: int, d: int, time: int, params: vt
 
 
 def vt_render_bwd(scene: int, n_rays: int, o: int, d: int, time: int, params: vt_render_params, rgb: int,
-                  rgb_residual: int, grad_rgb: int, grad_sites: int, grad_sigma: int, grad_tex: int, stream: int):
+                  rgb_residual: int, grad_rgb: int, grad_sites: int, grad_sigma: int, grad_tex: int,
+                  grad_tex_vd: int, stream: int):
     check(lib.vt_render_bwd(C.c_void_p(scene), n_rays, C.c_void_p(o), C.c_void_p(d), C.c_void_p(time),
                             C.byref(params), C.c_void_p(rgb), C.c_void_p(rgb_residual), C.c_void_p(grad_rgb),
-                            C.c_void_p(grad_sites), C.c_void_p(grad_sigma), C.c_void_p(grad_tex), C.c_void_p(stream)),
-          "vt_render_bwd")
+                            C.c_void_p(grad_sites), C.c_void_p(grad_sigma), C.c_void_p(grad_tex),
+                            C.c_void_p(grad_tex_vd), C.c_void_p(stream)), "vt_render_bwd")
 
 
 def vt_render_bwd_static(scene: int, n_rays: int, o: int, d: int, time: int, params: vt_render_params, rgb: int,

@@ -34,12 +34,16 @@ class Scene:
     """A Voronoi scene resident on the GPU (library-owned, Morton-ordered)."""
 
     def __init__(self, sites, sigma, tex, adj_offsets, adj_indices, tex_dtype="f32", device="cuda",
-                 keep_order=False):
+                 keep_order=False, tex_vd=None):
         device = torch.device(device)
         self.device = device
         sites = _dev_f32(sites, device)
         sigma = _dev_f32(sigma, device)
         tex = _dev_f32(tex, device)
+        tvd = None if tex_vd is None else _dev_f32(tex_vd, device)
+        if tvd is not None and tvd.shape != tex.shape:
+            raise ValueError("tex_vd must have the shape of tex")
+        self.has_tex_vd = tvd is not None
         off = torch.as_tensor(adj_offsets, dtype=torch.int64, device=device).contiguous()
         idx = torch.as_tensor(adj_indices, dtype=torch.int32, device=device).contiguous()
         n = sites.shape[0]
@@ -49,18 +53,19 @@ class Scene:
         self.n, self.R = n, tex.shape[1]
         self.tex_dtype = _DTYPES[tex_dtype] if isinstance(tex_dtype, str) else int(tex_dtype)
         desc = _vt.vt_scene_desc(n, self.R, self.tex_dtype, sites.data_ptr(), sigma.data_ptr(), tex.data_ptr(),
-                                 off.data_ptr(), idx.data_ptr(), _vt.VT_SCENE_KEEP_ORDER if keep_order else 0)
+                                 off.data_ptr(), idx.data_ptr(), _vt.VT_SCENE_KEEP_ORDER if keep_order else 0,
+                                 _ptr(tvd))
         with torch.cuda.device(device):
             self.handle = _vt.vt_scene_create(desc, _stream())
         self.n_edges = _vt.vt_scene_info(self.handle)[3]
 
     @classmethod
-    def from_workload(cls, sc, tex_dtype="f32", device="cuda", keep_order=False):
+    def from_workload(cls, sc, tex_dtype="f32", device="cuda", keep_order=False, tex_vd=None):
         return cls(sc.sites, sc.sigma, sc.tex, sc.offsets, sc.indices, tex_dtype=tex_dtype, device=device,
-                   keep_order=keep_order)
+                   keep_order=keep_order, tex_vd=tex_vd)
 
-    def update(self, sites=None, sigma=None, tex=None):
-        keep = [None if x is None else _dev_f32(x, self.device) for x in (sites, sigma, tex)]
+    def update(self, sites=None, sigma=None, tex=None, tex_vd=None):
+        keep = [None if x is None else _dev_f32(x, self.device) for x in (sites, sigma, tex, tex_vd)]
         _vt.vt_scene_update(self.handle, *[_ptr(x) for x in keep], _stream())
 
     def get_error(self):
@@ -80,7 +85,8 @@ class Scene:
 
 
 def make_params(t_near=0.0, t_far=20.0, use_clip_box=False, clip_lo=(0, 0, 0), clip_hi=(1, 1, 1), T_eps=1e-4,
-                skip_weight=0.0, bg=(1, 1, 1), img_w=0, img_h=0, n_images=0, max_steps=0, image_sizes=None):
+                skip_weight=0.0, bg=(1, 1, 1), img_w=0, img_h=0, n_images=0, max_steps=0, image_sizes=None,
+                appearance=0):
     """Render parameters. image_sizes: optional list of (w, h) per image for
     launches whose images differ in size (e.g. pinhole and 4-sample thin-lens
     views in one launch)."""
@@ -91,6 +97,7 @@ def make_params(t_near=0.0, t_far=20.0, use_clip_box=False, clip_lo=(0, 0, 0), c
     p.T_eps, p.skip_weight = T_eps, skip_weight
     p.bg[:] = list(bg)
     p.img_w, p.img_h, p.n_images, p.max_steps = img_w, img_h, n_images, max_steps
+    p.appearance = int(appearance)
     if image_sizes is not None:
         arr = (ctypes.c_int32 * (2 * len(image_sizes)))(*[int(v) for wh in image_sizes for v in wh])
         p._image_sizes_keepalive = arr  # the struct holds a raw pointer to it
@@ -143,7 +150,9 @@ def render_fwd(scene: Scene, o, d, params, time=None, out=None, want_steps=True,
 
 
 def render_bwd(scene: Scene, o, d, params, rgb, grad_rgb, time=None, out=None, need=(True, True, True),
-               residual=None):
+               residual=None, tex_vd_out=None):
+    """Backward render: (grad_sites, grad_sigma, grad_tex); the gradient of the
+    view-dependent texture (appearance 1) is written to `tex_vd_out` if given."""
     dev = o.device
     if out is None:
         gs = torch.empty(scene.n, 3, device=dev) if need[0] else None
@@ -152,7 +161,8 @@ def render_bwd(scene: Scene, o, d, params, rgb, grad_rgb, time=None, out=None, n
     else:
         gs, gsig, gt = out
     _vt.vt_render_bwd(scene.handle, o.shape[0], o.data_ptr(), d.data_ptr(), _ptr(time), params, rgb.data_ptr(),
-                      _ptr(residual), grad_rgb.contiguous().data_ptr(), _ptr(gs), _ptr(gsig), _ptr(gt), _stream())
+                      _ptr(residual), grad_rgb.contiguous().data_ptr(), _ptr(gs), _ptr(gsig), _ptr(gt),
+                      _ptr(tex_vd_out), _stream())
     return gs, gsig, gt
 
 
@@ -190,12 +200,12 @@ def average_samples_bwd(grad_px, spp):
 class VTRender(torch.autograd.Function):
     """Differentiable render of rays (o, d) through a Scene.
 
-    The scene's sites / sigma / tex tensors are passed so that autograd knows
-    which leaves receive gradients; the Scene must hold their current values
-    (call scene.update after changing them)."""
+    The scene's sites / sigma / tex (/ tex_vd for appearance 1) tensors are
+    passed so that autograd knows which leaves receive gradients; the Scene
+    must hold their current values (call scene.update after changing them)."""
 
     @staticmethod
-    def forward(ctx, sites, sigma, tex, o, d, scene, params):
+    def forward(ctx, sites, sigma, tex, tex_vd, o, d, scene, params):
         res = torch.empty(o.shape[0], 3, device=o.device)
         rgb, _, _ = render_fwd(scene, o, d, params, want_steps=False, residual=res)
         ctx.scene, ctx.params = scene, params
@@ -206,9 +216,13 @@ class VTRender(torch.autograd.Function):
     def backward(ctx, grad_rgb):
         o, d, rgb, res = ctx.saved_tensors
         need = ctx.needs_input_grad[:3]
-        gs, gsig, gt = render_bwd(ctx.scene, o, d, ctx.params, rgb, grad_rgb, need=need, residual=res)
-        return gs, gsig, gt, None, None, None, None
+        gvd = None
+        if ctx.needs_input_grad[3] and ctx.scene.has_tex_vd:
+            gvd = torch.empty(ctx.scene.n, ctx.scene.R, ctx.scene.R, 3, device=o.device)
+        gs, gsig, gt = render_bwd(ctx.scene, o, d, ctx.params, rgb, grad_rgb, need=need, residual=res,
+                                  tex_vd_out=gvd)
+        return gs, gsig, gt, gvd, None, None, None, None
 
 
-def render(sites, sigma, tex, o, d, scene: Scene, params):
-    return VTRender.apply(sites, sigma, tex, o, d, scene, params)
+def render(sites, sigma, tex, o, d, scene: Scene, params, tex_vd=None):
+    return VTRender.apply(sites, sigma, tex, tex_vd, o, d, scene, params)

@@ -37,6 +37,7 @@ struct vt_scene {
   vt_cell* cell = nullptr;
   float4* nbr = nullptr;
   void* tex = nullptr;
+  void* tex_vd = nullptr;  // view-dependent texture (appearance 1), same layout as tex
   int32_t* perm = nullptr;
   int32_t* inv = nullptr;
   // kernel-detected errors [0], FP64 recheck counter [1]
@@ -47,6 +48,7 @@ struct vt_scene {
   // backward scratch: per-cell {dL/ds_x, dL/ds_y, dL/ds_z, dL/dsigma}, per-texel RGBA
   float4* g_cell = nullptr;
   float4* g_tex = nullptr;
+  float4* g_tex_vd = nullptr;
 };
 
 static inline size_t vt_texel_bytes(int32_t dtype) { return dtype == VT_F32 ? 16 : 8; }

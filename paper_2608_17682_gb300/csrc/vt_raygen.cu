@@ -44,7 +44,7 @@ __global__ void k_raygen(CamBatch B, int64_t n_rays, float* __restrict__ O, floa
     while (c + 1 < B.n && ray >= B.first[c + 1]) ++c;
     const vt_camera& cam = B.cam[c];
     int64_t local = ray - B.first[c];
-    int S = cam.kind == VT_CAM_THIN_LENS ? cam.lens_samples : 1;
+    int S = (cam.kind == VT_CAM_THIN_LENS || cam.kind == VT_CAM_MOTION_BLUR) ? cam.lens_samples : 1;
     int s = (int)(local % S);
     int64_t pix = local / S;
     int y = (int)(pix / cam.w), x = (int)(pix - (int64_t)y * cam.w);
@@ -98,6 +98,11 @@ __global__ void k_raygen(CamBatch B, int64_t n_rays, float* __restrict__ O, floa
         o = add(eye, mul(cam.lens_radius, add(mul(lx, r), mul(ly, u))));
         float3 P = add(eye, mul(cam.focus_dist, pd));  // pd.f == 1: depth focus_dist
         d = make_float3(P.x - o.x, P.y - o.y, P.z - o.z);
+      } else if (cam.kind == VT_CAM_MOTION_BLUR) {
+        // stratified jittered time over the exposure, linear camera motion
+        const uint64_t cnt = (uint64_t)pix * S + s;
+        tm = ((float)s + uniform24(cam.seed, cnt << 1)) / (float)S;
+        o = add(o, mul(tm, f3(cam.rs_velocity)));
       }
     }
     d = unit(d);
@@ -148,7 +153,8 @@ __global__ void k_avg_bwd(int64_t n, int spp, const float* __restrict__ g, float
 }
 
 bool camera_ok(const vt_camera& c) {
-  if (c.w <= 0 || c.h <= 0 || c.kind < 0 || c.kind > 3) return false;
+  if (c.w <= 0 || c.h <= 0 || c.kind < 0 || c.kind > 4) return false;
+  if (c.kind == VT_CAM_MOTION_BLUR && c.lens_samples < 1) return false;
   float fl = sqrtf(c.fwd[0] * c.fwd[0] + c.fwd[1] * c.fwd[1] + c.fwd[2] * c.fwd[2]);
   if (!(fl > 0.f)) return false;
   if (c.kind == VT_CAM_THIN_LENS) {
@@ -165,7 +171,8 @@ extern "C" {
 
 int64_t vt_camera_n_rays(const vt_camera* c) {
   if (!c) return 0;
-  return (int64_t)c->w * c->h * (c->kind == VT_CAM_THIN_LENS ? c->lens_samples : 1);
+  const bool multi = c->kind == VT_CAM_THIN_LENS || c->kind == VT_CAM_MOTION_BLUR;
+  return (int64_t)c->w * c->h * (multi ? c->lens_samples : 1);
 }
 
 vt_status vt_generate_rays(const vt_camera* cams, int32_t n_cams, float* o, float* d, float* time, void* stream) {

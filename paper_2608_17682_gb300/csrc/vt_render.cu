@@ -50,11 +50,22 @@ enum Mode { FWD = 0, BWD = 1, TRACE = 2 };
 #ifndef VT_AGG
 #define VT_AGG 0
 #endif
+// 1: the backward re-reads the previous cell's position from its record
+// instead of keeping it in registers across the neighbour loop
+#ifndef VT_BWD_RELOAD_PREV
+#define VT_BWD_RELOAD_PREV 1
+#endif
+// unroll factor of the neighbour loop
+#ifndef VT_NBR_UNROLL
+#define VT_NBR_UNROLL 8
+#endif
+constexpr int kNbrUnroll = VT_NBR_UNROLL;
 
 struct Scene {
   const vt_cell* __restrict__ cell;
   const float4* __restrict__ nbr;
   const void* __restrict__ tex;
+  const void* __restrict__ tex_vd;
   int64_t n;
   int32_t R, RR;
   unsigned long long* err;
@@ -76,6 +87,7 @@ struct RP {  // render parameters, device copy
   int max_steps;
   int64_t n_rays;
   int64_t anchor_stride;
+  int appearance;
   // ray layout: 0 plain 1-D, 1 n_images equal images, 2 table of images
   int layout, n_tab;
   int64_t total_tiles;
@@ -90,6 +102,7 @@ __device__ __forceinline__ int64_t anchor_ray(const RP& P, int a) {
 struct Grad {
   float4* g_cell;
   float4* g_tex;
+  float4* g_tex_vd;
   const float* rgb;
   const float* rgb_lo;  // optional residual of the forward colour
   const float* grad;
@@ -180,6 +193,7 @@ __device__ __forceinline__ float3 texel_rgb(const TexRaw<DT>& t) {
 struct Taps {
   int base, sx, sy;
   float fx, fy;
+  float gxs, gys;  // d(texel x, y)/d(u, v): R/2 inside, 0 where clamped
 };
 
 __device__ __forceinline__ Taps taps_for(float3 d, int R) {
@@ -195,10 +209,12 @@ __device__ __forceinline__ Taps taps_for(float3 d, int R) {
   }
   float x = __fsub_rn(__fmul_rn(__fmul_rn(__fadd_rn(u, 1.f), 0.5f), (float)R), 0.5f);
   float y = __fsub_rn(__fmul_rn(__fmul_rn(__fadd_rn(v, 1.f), 0.5f), (float)R), 0.5f);
+  Taps t;
+  t.gxs = (x >= 0.f && x <= (float)(R - 1)) ? 0.5f * (float)R : 0.f;
+  t.gys = (y >= 0.f && y <= (float)(R - 1)) ? 0.5f * (float)R : 0.f;
   x = fminf(fmaxf(x, 0.f), (float)(R - 1));
   y = fminf(fmaxf(y, 0.f), (float)(R - 1));
   int x0 = min((int)floorf(x), R - 1), y0 = min((int)floorf(y), R - 1);
-  Taps t;
   t.base = y0 * R + x0;
   t.sx = x0 + 1 < R ? 1 : 0;
   t.sy = y0 + 1 < R ? R : 0;
@@ -213,6 +229,25 @@ __device__ __forceinline__ void tap_weights(const Taps& t, float w[4]) {
   w[1] = __fmul_rn(t.fx, gy);
   w[2] = __fmul_rn(gx, t.fy);
   w[3] = __fmul_rn(t.fx, t.fy);
+}
+
+// (gu, gv) . d(u, v)/d(dir) for the octahedral map (Sec. 5.1) of `dir`
+__device__ __forceinline__ float3 oct_vjp(float3 dir, float gu, float gv) {
+  const float l1 = fabsf(dir.x) + fabsf(dir.y) + fabsf(dir.z);
+  const float il = 1.f / l1;
+  const float qx = dir.x * il, qy = dir.y * il;
+  const float sx = dir.x >= 0.f ? 1.f : -1.f, sy = dir.y >= 0.f ? 1.f : -1.f, sz = dir.z >= 0.f ? 1.f : -1.f;
+  // dq_a/ddir_j = (delta_aj - q_a sgn(dir_j)) / l1
+  float ax, ay;  // coefficients on dq_x and dq_y
+  if (dir.z >= 0.f) {
+    ax = gu;
+    ay = gv;
+  } else {
+    ax = -sy * sx * gv;
+    ay = -sx * sy * gu;
+  }
+  const float dot = ax * qx + ay * qy;
+  return make_float3((ax - dot * sx) * il, (ay - dot * sy) * il, -dot * sz * il);
 }
 
 // n.d for n = sj - si: plain FP32 when the crossing is not near grazing
@@ -453,7 +488,7 @@ struct WalkBounds {
   static constexpr int minb = MODE == FWD ? VT_FWD_MINB : (MODE == BWD ? VT_BWD_MINB : 2);
 };
 
-template <int MODE, int DT>
+template <int MODE, int DT, int APP>
 __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
     k_walk(Scene S, RP P, const float* __restrict__ O, const float* __restrict__ D,
            const int32_t* __restrict__ anchor_cell, float* __restrict__ rgb_out, float* __restrict__ T_out,
@@ -488,7 +523,8 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
   if (bad) {
     atomicOr(S.err, (unsigned long long)VT_EBIT_BAD_RAY);
   } else if (t1 > t0) {
-    const Taps tp = taps_for(d, S.R);
+    // taps of the ray direction (appearance 0) / of the view direction -d (T_vd, appearance 1)
+    const Taps tp = taps_for(APP ? make_float3(-d.x, -d.y, -d.z) : d, S.R);
     const float Gd = __fmul_rn(1e-6f, sqrtf(dd));  // grazing scale 1e-6 |d|
     // BWD: g = dL/dC and the suffix S_k = C_out - sum_{m<=k} w_m c_m as float-float
     float g0 = 0.f, g1 = 0.f, g2 = 0.f, Sh0 = 0.f, Sh1 = 0.f, Sh2 = 0.f, Sl0 = 0.f, Sl1 = 0.f, Sl2 = 0.f;
@@ -524,6 +560,7 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
     float p_sdtau = 0.f, p_gsig = 0.f;
     float3 p_gs = make_float3(0.f, 0.f, 0.f), p_s = make_float3(0.f, 0.f, 0.f);
     bool cross_valid = false;
+    float p_xt = 0.f;  // appearance 1: colour term dL/dt pending on the previous cell's exit crossing
     for (;;) {
       if (k >= P.max_steps) {
         atomicOr(S.err, (unsigned long long)VT_EBIT_MAX_STEPS);
@@ -536,7 +573,7 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
       // texels of this cell (independent of the exit search)
       TexRaw<DT> tx0, tx1, tx2, tx3;
       const int64_t tb0 = (int64_t)cell * S.RR + tp.base;
-      if (MODE != TRACE && VT_TEX_EARLY) {
+      if (MODE != TRACE && VT_TEX_EARLY && !APP) {
         tx0 = load_texel<DT>(S.tex, tb0);
         tx1 = load_texel<DT>(S.tex, tb0 + tp.sx);
         tx2 = load_texel<DT>(S.tex, tb0 + tp.sy);
@@ -549,7 +586,7 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
       const float Gc = __fmul_rn(Gd, __int_as_float(m.w));
       float bn = 1.f, bd = 0.f;  // best dt = bn / bd (bd == 0: none yet)
       int bj = -1;
-#pragma unroll 2
+#pragma unroll kNbrUnroll
       for (int p = m.x; p < m.y; ++p) {
         const float4 q = __ldg(S.nbr + p);
         float den = __fmaf_rn(q.x, d.x, __fmaf_rn(q.y, d.y, __fmul_rn(q.z, d.z)));
@@ -571,7 +608,7 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
         }
       }
       ++k;
-      if (MODE != TRACE && !VT_TEX_EARLY) {
+      if (MODE != TRACE && !VT_TEX_EARLY && !APP) {
         tx0 = load_texel<DT>(S.tex, tb0);
         tx1 = load_texel<DT>(S.tex, tb0 + tp.sx);
         tx2 = load_texel<DT>(S.tex, tb0 + tp.sy);
@@ -606,6 +643,14 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
       float dtau = 0.f, w = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
       bool coloured = false;
       float tw[4];
+      // appearance 1: surface direction, its taps, and the colour gradient terms
+      float3 dsurf = make_float3(0.f, 0.f, 0.f);
+      float rlen = 0.f, gt_col = 0.f;
+      float3 gx_col = make_float3(0.f, 0.f, 0.f);
+      Taps tv{0, 0, 0, 0.f, 0.f, 0.f, 0.f};
+      float wv[4] = {0.f, 0.f, 0.f, 0.f};
+      int64_t tbv = 0;
+      float gz0 = 0.f, gz1 = 0.f, gz2 = 0.f;
       if (delta > 0.f) {
         const float e = __expf(-__fmul_rn(sig, delta));
         const float alpha = __fsub_rn(1.f, e);
@@ -614,11 +659,66 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
         if (MODE != TRACE && (!(P.skip > 0.f) || w >= P.skip)) {
           coloured = true;
           tap_weights(tp, tw);
-          const float3 a0 = texel_rgb<DT>(tx0), a1 = texel_rgb<DT>(tx1), a2 = texel_rgb<DT>(tx2),
-                       a3 = texel_rgb<DT>(tx3);
-          c0 = __fmaf_rn(tw[3], a3.x, __fmaf_rn(tw[2], a2.x, __fmaf_rn(tw[1], a1.x, __fmul_rn(tw[0], a0.x))));
-          c1 = __fmaf_rn(tw[3], a3.y, __fmaf_rn(tw[2], a2.y, __fmaf_rn(tw[1], a1.y, __fmul_rn(tw[0], a0.y))));
-          c2 = __fmaf_rn(tw[3], a3.z, __fmaf_rn(tw[2], a2.z, __fmaf_rn(tw[1], a1.z, __fmul_rn(tw[0], a0.z))));
+          if constexpr (APP == 0) {
+            const float3 a0 = texel_rgb<DT>(tx0), a1 = texel_rgb<DT>(tx1), a2 = texel_rgb<DT>(tx2),
+                         a3 = texel_rgb<DT>(tx3);
+            c0 = __fmaf_rn(tw[3], a3.x, __fmaf_rn(tw[2], a2.x, __fmaf_rn(tw[1], a1.x, __fmul_rn(tw[0], a0.x))));
+            c1 = __fmaf_rn(tw[3], a3.y, __fmaf_rn(tw[2], a2.y, __fmaf_rn(tw[1], a1.y, __fmul_rn(tw[0], a0.y))));
+            c2 = __fmaf_rn(tw[3], a3.z, __fmaf_rn(tw[2], a2.z, __fmaf_rn(tw[1], a1.z, __fmul_rn(tw[0], a0.z))));
+          } else {
+            // Sec. 5.1-5.2: x = entry point (origin cell: exit point, or segment end)
+            float3 vs;
+            if (k > 1) {
+              vs = make_float3(-r.x, -r.y, -r.z);
+            } else {
+              const float tx = bj >= 0 ? dt : __fsub_rn(t1, th);
+              vs = make_float3(__fmaf_rn(tx, d.x, -r.x), __fmaf_rn(tx, d.y, -r.y), __fmaf_rn(tx, d.z, -r.z));
+            }
+            rlen = sqrtf(vs.x * vs.x + vs.y * vs.y + vs.z * vs.z);
+            const float il = rlen > 0.f ? 1.f / rlen : rsqrtf(dd);
+            dsurf = rlen > 0.f ? make_float3(vs.x * il, vs.y * il, vs.z * il) : make_float3(d.x * il, d.y * il, d.z * il);
+            tv = taps_for(dsurf, S.R);
+            tap_weights(tv, wv);
+            tbv = (int64_t)cell * S.RR + tv.base;
+            const int64_t tbd = tb0;  // view-dependent taps of this cell
+            const float3 a0 = texel_rgb<DT>(load_texel<DT>(S.tex, tbv));
+            const float3 a1 = texel_rgb<DT>(load_texel<DT>(S.tex, tbv + tv.sx));
+            const float3 a2 = texel_rgb<DT>(load_texel<DT>(S.tex, tbv + tv.sy));
+            const float3 a3 = texel_rgb<DT>(load_texel<DT>(S.tex, tbv + tv.sx + tv.sy));
+            const float3 b0 = texel_rgb<DT>(load_texel<DT>(S.tex_vd, tbd));
+            const float3 b1 = texel_rgb<DT>(load_texel<DT>(S.tex_vd, tbd + tp.sx));
+            const float3 b2 = texel_rgb<DT>(load_texel<DT>(S.tex_vd, tbd + tp.sy));
+            const float3 b3 = texel_rgb<DT>(load_texel<DT>(S.tex_vd, tbd + tp.sx + tp.sy));
+            const float z0 = wv[0] * a0.x + wv[1] * a1.x + wv[2] * a2.x + wv[3] * a3.x + tw[0] * b0.x + tw[1] * b1.x +
+                             tw[2] * b2.x + tw[3] * b3.x;
+            const float z1 = wv[0] * a0.y + wv[1] * a1.y + wv[2] * a2.y + wv[3] * a3.y + tw[0] * b0.y + tw[1] * b1.y +
+                             tw[2] * b2.y + tw[3] * b3.y;
+            const float z2 = wv[0] * a0.z + wv[1] * a1.z + wv[2] * a2.z + wv[3] * a3.z + tw[0] * b0.z + tw[1] * b1.z +
+                             tw[2] * b2.z + tw[3] * b3.z;
+            c0 = 1.f / (1.f + __expf(-z0));
+            c1 = 1.f / (1.f + __expf(-z1));
+            c2 = 1.f / (1.f + __expf(-z2));
+            if (MODE == BWD) {
+              // dL/dz = g w c (1 - c); through the bilinear fetch and the octahedral
+              // map into the surface direction, then into x and the site
+              gz0 = g0 * w * c0 * (1.f - c0);
+              gz1 = g1 * w * c1 * (1.f - c1);
+              gz2 = g2 * w * c2 * (1.f - c2);
+              const float gu = tv.gxs * (gz0 * ((1.f - tv.fy) * (a1.x - a0.x) + tv.fy * (a3.x - a2.x)) +
+                                         gz1 * ((1.f - tv.fy) * (a1.y - a0.y) + tv.fy * (a3.y - a2.y)) +
+                                         gz2 * ((1.f - tv.fy) * (a1.z - a0.z) + tv.fy * (a3.z - a2.z)));
+              const float gv = tv.gys * (gz0 * ((1.f - tv.fx) * (a2.x - a0.x) + tv.fx * (a3.x - a1.x)) +
+                                         gz1 * ((1.f - tv.fx) * (a2.y - a0.y) + tv.fx * (a3.y - a1.y)) +
+                                         gz2 * ((1.f - tv.fx) * (a2.z - a0.z) + tv.fx * (a3.z - a1.z)));
+              const float3 gd = oct_vjp(dsurf, gu, gv);
+              if (rlen > 0.f) {
+                const float dg = gd.x * dsurf.x + gd.y * dsurf.y + gd.z * dsurf.z;
+                gx_col = make_float3((gd.x - dsurf.x * dg) / rlen, (gd.y - dsurf.y * dg) / rlen,
+                                     (gd.z - dsurf.z * dg) / rlen);
+                gt_col = gx_col.x * d.x + gx_col.y * d.y + gx_col.z * d.z;
+              }
+            }
+          }
           if (MODE == FWD) {
             ff_fma_acc(Ch0, Cl0, w, c0, 1.f);
             ff_fma_acc(Ch1, Cl1, w, c1, 1.f);
@@ -638,40 +738,68 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
       }
       if (MODE == BWD) {
         // crossing between the previous cell and this one (entry face):
-        // dL/dt_b = sigma_prev dtau_prev - sigma dtau; x_b - s_prev = n - r, s_cur - x_b = r
+        // dL/dt_b = sigma_prev dtau_prev - sigma dtau (inside the extent)
+        //           + colour terms of surface points on this face (appearance 1);
+        // x_b - s_prev = n - r, s_cur - x_b = r
         float3 gs = make_float3(0.f, 0.f, 0.f);
-        if (pc >= 0 && cross_valid) {
+        float dLdt = cross_valid ? p_sdtau - sig * dtau : 0.f;
+        if (APP) dLdt += p_xt + (k > 1 ? gt_col : 0.f);
+        if (pc >= 0 && dLdt != 0.f) {
+#if VT_BWD_RELOAD_PREV
+          {  // previous site from its record (L1-resident) instead of a live register triple
+            const float4 pp = cell_pos(S.cell, pc);
+            p_s = make_float3(pp.x, pp.y, pp.z);
+          }
+#endif
           const float nd = crossing_nd(p_s, si, d, dd);
-          const float dtb = __fdividef(p_sdtau - sig * dtau, nd);
+          const float dtb = __fdividef(dLdt, nd);
           const float nx = __fsub_rn(si.x, p_s.x), ny = __fsub_rn(si.y, p_s.y), nz = __fsub_rn(si.z, p_s.z);
           p_gs.x += dtb * (nx - r.x);
           p_gs.y += dtb * (ny - r.y);
           p_gs.z += dtb * (nz - r.z);
           gs = make_float3(dtb * r.x, dtb * r.y, dtb * r.z);
         }
+        if (APP) {  // the site itself moves the surface direction
+          gs.x -= gx_col.x;
+          gs.y -= gx_col.y;
+          gs.z -= gx_col.z;
+        }
         if (pc >= 0) add_cell_grad(G.g_cell, pc, p_gs.x, p_gs.y, p_gs.z, p_gsig);
-        if (coloured && w > 0.f)
-          add_tex_grad(G.g_tex, tb0, tp.sx, tp.sy, g0, g1, g2, w, tw, S.n * S.RR < ((int64_t)1 << 31));
+        if (coloured && w > 0.f) {
+          if constexpr (APP == 0) {
+            add_tex_grad(G.g_tex, tb0, tp.sx, tp.sy, g0, g1, g2, w, tw, S.n * S.RR < ((int64_t)1 << 31));
+          } else {
+            add_tex_grad(G.g_tex, tbv, tv.sx, tv.sy, gz0, gz1, gz2, 1.f, wv, S.n * S.RR < ((int64_t)1 << 31));
+            add_tex_grad(G.g_tex_vd, tb0, tp.sx, tp.sy, gz0, gz1, gz2, 1.f, tw, S.n * S.RR < ((int64_t)1 << 31));
+          }
+        }
         pc = cell;
         p_sdtau = sig * dtau;
         p_gsig = dtau * delta;
         p_gs = gs;
+#if !VT_BWD_RELOAD_PREV
         p_s = si;
+#endif
         // will the crossing at this cell's exit be differentiable?
         cross_valid = (bj >= 0) && !exit_beyond && ff_gt(eh, el, t0);
-        if (stop && cross_valid) {
-          // terminated inside the extent: the exit plane still moves delta_K
+        // appearance 1: the origin cell's colour sits on its exit crossing
+        const float xt_exit = (APP && k == 1 && bj >= 0) ? gt_col : 0.f;
+        const float dLdt_exit = (stop && cross_valid ? p_sdtau : 0.f) + xt_exit;
+        if ((stop || exit_beyond) && bj >= 0 && dLdt_exit != 0.f) {
+          // the walk ends in this cell but its exit plane still moves delta_K
+          // (terminated inside the extent) and/or its surface point
           const float4 q4 = cell_pos(S.cell, bj);
           const float3 sj = make_float3(q4.x, q4.y, q4.z);
           const float3 re = rel_pos(si, o, d, eh, el);  // s_K - x_out
           const float nd = crossing_nd(si, sj, d, dd);
-          const float dtb = __fdividef(p_sdtau, nd);
+          const float dtb = __fdividef(dLdt_exit, nd);
           const float nx = __fsub_rn(sj.x, si.x), ny = __fsub_rn(sj.y, si.y), nz = __fsub_rn(sj.z, si.z);
           p_gs.x -= dtb * re.x;
           p_gs.y -= dtb * re.y;
           p_gs.z -= dtb * re.z;
           add_cell_grad(G.g_cell, bj, dtb * (re.x + nx), dtb * (re.y + ny), dtb * (re.z + nz), 0.f);
         }
+        p_xt = xt_exit;
       }
       if (stop || exit_beyond) break;
       cell = bj;
@@ -710,7 +838,8 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
 
 // user-order gradients from the Morton-ordered scratch (overwrites outputs)
 __global__ void k_grad_out(int64_t n, int RR, const vt_cell* __restrict__ cells, const float4* __restrict__ g_cell,
-                           const float4* __restrict__ g_tex, float* gs, float* gsig, float* gtex) {
+                           const float4* __restrict__ g_tex, float* gs, float* gsig, float* gtex,
+                           const float4* __restrict__ g_tex_vd = nullptr, float* gtex_vd = nullptr) {
   int64_t total = n * RR;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = e / RR, t = e - i * RR;
@@ -718,6 +847,13 @@ __global__ void k_grad_out(int64_t n, int RR, const vt_cell* __restrict__ cells,
     if (gtex) {
       float4 g = g_tex[e];
       float* dst = gtex + (u * RR + t) * 3;
+      dst[0] = g.x;
+      dst[1] = g.y;
+      dst[2] = g.z;
+    }
+    if (gtex_vd) {
+      float4 g = g_tex_vd[e];
+      float* dst = gtex_vd + (u * RR + t) * 3;
       dst[0] = g.x;
       dst[1] = g.y;
       dst[2] = g.z;
@@ -745,6 +881,9 @@ vt_status make_rp(const vt_scene* s, int64_t n_rays, const vt_render_params* p, 
   P.T_eps = p->T_eps;
   P.skip = p->skip_weight;
   P.bg = make_float3(p->bg[0], p->bg[1], p->bg[2]);
+  P.appearance = p->appearance;
+  if (p->appearance != 0 && p->appearance != 1) return VT_ERR_INVALID_ARG;
+  if (p->appearance == 1 && !s->tex_vd) return VT_ERR_INVALID_ARG;
   P.img_w = p->img_w;
   P.img_h = p->img_h;
   P.n_images = p->n_images;
@@ -815,6 +954,7 @@ Scene scene_view(vt_scene* s) {
   S.cell = s->cell;
   S.nbr = s->nbr;
   S.tex = s->tex;
+  S.tex_vd = s->tex_vd;
   S.n = s->n;
   S.R = s->R;
   S.RR = s->R * s->R;
@@ -833,18 +973,27 @@ vt_status anchors(vt_scene* s, const Scene& S, const RP& P, const float* o, cuda
   return VT_OK;
 }
 
+template <int MODE, int APP>
+void launch_walk_app(vt_scene* s, const Scene& S, const RP& P, const float* o, const float* d, float* rgb, float* T,
+                     int32_t* steps, Grad G, Trace TR, cudaStream_t st, int g) {
+  if (s->dtype == VT_F32)
+    k_walk<MODE, VT_F32, APP><<<g, 256, 0, st>>>(S, P, o, d, s->anchor_cell, rgb, T, steps, G, TR);
+  else if (s->dtype == VT_F16)
+    k_walk<MODE, VT_F16, APP><<<g, 256, 0, st>>>(S, P, o, d, s->anchor_cell, rgb, T, steps, G, TR);
+  else
+    k_walk<MODE, VT_BF16, APP><<<g, 256, 0, st>>>(S, P, o, d, s->anchor_cell, rgb, T, steps, G, TR);
+}
+
 template <int MODE>
 vt_status launch_walk(vt_scene* s, const Scene& S, const RP& P, const float* o, const float* d, float* rgb,
                       float* T, int32_t* steps, Grad G, Trace TR, cudaStream_t st) {
   int64_t nt = walk_threads(P);
   if (nt == 0) return VT_OK;
   int g = vt_grid(nt, 256, ((int64_t)1 << 31) - 1);
-  if (s->dtype == VT_F32)
-    k_walk<MODE, VT_F32><<<g, 256, 0, st>>>(S, P, o, d, s->anchor_cell, rgb, T, steps, G, TR);
-  else if (s->dtype == VT_F16)
-    k_walk<MODE, VT_F16><<<g, 256, 0, st>>>(S, P, o, d, s->anchor_cell, rgb, T, steps, G, TR);
+  if (MODE != TRACE && P.appearance == 1)
+    launch_walk_app<MODE, MODE == TRACE ? 0 : 1>(s, S, P, o, d, rgb, T, steps, G, TR, st, g);
   else
-    k_walk<MODE, VT_BF16><<<g, 256, 0, st>>>(S, P, o, d, s->anchor_cell, rgb, T, steps, G, TR);
+    launch_walk_app<MODE, 0>(s, S, P, o, d, rgb, T, steps, G, TR, st, g);
   VT_CUDA_TRY(cudaGetLastError());
   return VT_OK;
 }
@@ -874,9 +1023,10 @@ vt_status vt_render_fwd(vt_scene* s, int64_t n_rays, const float* o, const float
 vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float* d, const float* time,
                         const vt_render_params* p, const float* rgb_out, const float* rgb_residual,
                         const float* grad_rgb, float* grad_sites, float* grad_sigma, float* grad_tex,
-                        void* stream) {
+                        float* grad_tex_vd, void* stream) {
   (void)time;
   if (!s || n_rays < 0 || (n_rays > 0 && (!o || !d || !rgb_out || !grad_rgb))) return VT_ERR_INVALID_ARG;
+  if (grad_tex_vd && !s->tex_vd) return VT_ERR_INVALID_ARG;
   RP P;
   vt_status r = make_rp(s, n_rays > 0 ? n_rays : 0, p, P);
   if (r != VT_OK && n_rays > 0) return r;
@@ -884,19 +1034,22 @@ vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float
   const int64_t RR = (int64_t)s->R * s->R;
   if (!s->g_cell) VT_CUDA_TRY(cudaMalloc(&s->g_cell, s->n * sizeof(float4)));
   if (!s->g_tex) VT_CUDA_TRY(cudaMalloc(&s->g_tex, s->n * RR * sizeof(float4)));
+  if (s->tex_vd && !s->g_tex_vd) VT_CUDA_TRY(cudaMalloc(&s->g_tex_vd, s->n * RR * sizeof(float4)));
   VT_CUDA_TRY(cudaMemsetAsync(s->g_cell, 0, s->n * sizeof(float4), st));
   VT_CUDA_TRY(cudaMemsetAsync(s->g_tex, 0, s->n * RR * sizeof(float4), st));
+  if (s->g_tex_vd) VT_CUDA_TRY(cudaMemsetAsync(s->g_tex_vd, 0, s->n * RR * sizeof(float4), st));
   Scene S = scene_view(s);
   if (n_rays > 0) {
     r = anchors(s, S, P, o, st);
     if (r != VT_OK) return r;
-    Grad G{s->g_cell, s->g_tex, rgb_out, rgb_residual, grad_rgb};
+    Grad G{s->g_cell, s->g_tex, s->g_tex_vd, rgb_out, rgb_residual, grad_rgb};
     r = launch_walk<BWD>(s, S, P, o, d, nullptr, nullptr, nullptr, G, Trace{}, st);
     if (r != VT_OK) return r;
   }
-  if (grad_sites || grad_sigma || grad_tex) {
+  if (grad_sites || grad_sigma || grad_tex || grad_tex_vd) {
     k_grad_out<<<vt_grid(s->n * RR, 256, 152 * 64), 256, 0, st>>>(s->n, (int)RR, s->cell, s->g_cell, s->g_tex,
-                                                                    grad_sites, grad_sigma, grad_tex);
+                                                                    grad_sites, grad_sigma, grad_tex, s->g_tex_vd,
+                                                                    grad_tex_vd);
     VT_CUDA_TRY(cudaGetLastError());
   }
   return VT_OK;
@@ -960,6 +1113,7 @@ vt_status vt_render_bwd_static(vt_scene* s, int64_t n_rays, const float* o, cons
                                float* grad_sites, float* grad_sigma, float* grad_tex, void* stream) {
   (void)time;
   if (!s || n_rays < 0 || (n_rays > 0 && (!o || !d || !rgb_out || !grad_rgb))) return VT_ERR_INVALID_ARG;
+  if (p && p->appearance != 0) return VT_ERR_UNSUPPORTED;
   const int64_t RR = (int64_t)s->R * s->R;
   const int64_t need = s->n * (1 + RR);  // one float4 per cell + one per texel
   if (need > kStaticScratchFloat4) return VT_ERR_CAPACITY;
@@ -978,7 +1132,7 @@ vt_status vt_render_bwd_static(vt_scene* s, int64_t n_rays, const float* o, cons
   if (n_rays > 0) {
     r = anchors(s, S, P, o, st);
     if (r != VT_OK) return r;
-    Grad G{g_cell, g_tex, rgb_out, nullptr, grad_rgb};
+    Grad G{g_cell, g_tex, nullptr, rgb_out, nullptr, grad_rgb};
     r = launch_walk<BWD>(s, S, P, o, d, nullptr, nullptr, nullptr, G, Trace{}, st);
     if (r != VT_OK) return r;
   }

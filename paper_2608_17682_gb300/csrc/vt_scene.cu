@@ -210,15 +210,16 @@ __global__ void k_pack_tex(int64_t n, int32_t RR, const int32_t* __restrict__ pe
   }
 }
 
-vt_status pack_tex(vt_scene* s, const float* tex, cudaStream_t st) {
+vt_status pack_tex(vt_scene* s, const float* tex, cudaStream_t st, void* dst = nullptr) {
   int64_t total = s->n * (int64_t)s->R * s->R;
   int g = vt_grid(total, 256, 152 * 64);
+  void* out = dst ? dst : s->tex;
   if (s->dtype == VT_F32)
-    k_pack_tex<VT_F32><<<g, 256, 0, st>>>(s->n, s->R * s->R, s->perm, tex, s->tex);
+    k_pack_tex<VT_F32><<<g, 256, 0, st>>>(s->n, s->R * s->R, s->perm, tex, out);
   else if (s->dtype == VT_F16)
-    k_pack_tex<VT_F16><<<g, 256, 0, st>>>(s->n, s->R * s->R, s->perm, tex, s->tex);
+    k_pack_tex<VT_F16><<<g, 256, 0, st>>>(s->n, s->R * s->R, s->perm, tex, out);
   else
-    k_pack_tex<VT_BF16><<<g, 256, 0, st>>>(s->n, s->R * s->R, s->perm, tex, s->tex);
+    k_pack_tex<VT_BF16><<<g, 256, 0, st>>>(s->n, s->R * s->R, s->perm, tex, out);
   VT_CUDA_TRY(cudaGetLastError());
   return VT_OK;
 }
@@ -257,6 +258,7 @@ void free_scene(vt_scene* s) {
   cudaFree(s->cell);
   cudaFree(s->nbr);
   cudaFree(s->tex);
+  cudaFree(s->tex_vd);
   cudaFree(s->perm);
   cudaFree(s->inv);
   cudaFree(s->d_err);
@@ -264,6 +266,7 @@ void free_scene(vt_scene* s) {
   cudaFree(s->anchor_cell);
   cudaFree(s->g_cell);
   cudaFree(s->g_tex);
+  cudaFree(s->g_tex_vd);
   delete s;
 }
 
@@ -285,6 +288,7 @@ vt_status create_impl(const vt_scene_desc* dsc, cudaStream_t st, vt_scene* s) {
   VT_CUDA_TRY(dmalloc(&s->cell, n));
   VT_CUDA_TRY(dmalloc(&s->nbr, E > 0 ? E : 1));
   VT_CUDA_TRY(cudaMalloc(&s->tex, n * RR * vt_texel_bytes(s->dtype) + 16));
+  if (dsc->tex_vd) VT_CUDA_TRY(cudaMalloc(&s->tex_vd, n * RR * vt_texel_bytes(s->dtype) + 16));
   VT_CUDA_TRY(dmalloc(&s->perm, n));
   VT_CUDA_TRY(dmalloc(&s->inv, n));
   VT_CUDA_TRY(dmalloc(&s->d_err, 4));
@@ -357,6 +361,10 @@ vt_status create_impl(const vt_scene_desc* dsc, cudaStream_t st, vt_scene* s) {
     k_cell_nmax<<<g, 256, 0, st>>>(n, s->cell, s->nbr);
     rs = pack_tex(s, dsc->tex, st);
     if (rs != VT_OK) break;
+    if (dsc->tex_vd) {
+      rs = pack_tex(s, dsc->tex_vd, st, s->tex_vd);
+      if (rs != VT_OK) break;
+    }
     if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) rs = VT_ERR_CUDA;
   } while (0);
   cudaFree(code);
@@ -420,8 +428,9 @@ vt_status vt_scene_create(const vt_scene_desc* dsc, void* stream, vt_scene** out
   return VT_OK;
 }
 
-vt_status vt_scene_update(vt_scene* s, const float* sites, const float* sigma, const float* tex, void* stream) {
-  if (!s) return VT_ERR_INVALID_ARG;
+vt_status vt_scene_update(vt_scene* s, const float* sites, const float* sigma, const float* tex,
+                          const float* tex_vd, void* stream) {
+  if (!s || (tex_vd && !s->tex_vd)) return VT_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   if (sites || sigma) {
     vt_status v = validate(s->n, sites, sigma, nullptr, nullptr, 0, st);
@@ -436,6 +445,10 @@ vt_status vt_scene_update(vt_scene* s, const float* sites, const float* sigma, c
   }
   if (tex) {
     vt_status v = pack_tex(s, tex, st);
+    if (v != VT_OK) return v;
+  }
+  if (tex_vd) {
+    vt_status v = pack_tex(s, tex_vd, st, s->tex_vd);
     if (v != VT_OK) return v;
   }
   return VT_OK;

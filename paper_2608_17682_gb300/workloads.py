@@ -182,7 +182,8 @@ def orbit_eye(target, radius, az_deg, el_deg):
 class Camera:
     """Camera description, mirrored by the C ABI's ``vt_camera``.
 
-    kind: 0 pinhole, 1 equidistant fisheye, 2 rolling shutter, 3 thin lens."""
+    kind: 0 pinhole, 1 equidistant fisheye, 2 rolling shutter, 3 thin lens,
+    4 motion blur (lens_samples time samples per pixel)."""
 
     kind: int
     w: int
@@ -199,8 +200,12 @@ class Camera:
     seed: int = 0
 
     @property
+    def spp(self):
+        return self.lens_samples if self.kind in (3, 4) else 1
+
+    @property
     def n_rays(self):
-        return self.w * self.h * (self.lens_samples if self.kind == 3 else 1)
+        return self.w * self.h * self.spp
 
 
 def look_at_camera(kind, w, h, eye, target, **kw) -> Camera:

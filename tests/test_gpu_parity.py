@@ -276,7 +276,7 @@ def test_l2_loss_kernel(tiny):
 
 # ---------------------------------------------------------------- ray generation
 
-@pytest.mark.parametrize("kind", [0, 1, 2, 3])
+@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4])
 def test_raygen_parity(kind):
     eye = W.orbit_eye(np.zeros(3), 3.0, 67.5, 20.0)
     kw = {}
@@ -284,6 +284,8 @@ def test_raygen_parity(kind):
         kw = dict(rs_velocity=(0.05, -0.02, 0.0))
     if kind == 3:
         kw = dict(lens_radius=0.01, focus_dist=3.0, lens_samples=4, seed=4242)
+    if kind == 4:
+        kw = dict(rs_velocity=(0.03, 0.01, -0.02), lens_samples=3, seed=99)
     cam = W.look_at_camera(kind, 130, 83, eye, np.zeros(3), **kw)
     o, d, t = api.generate_rays([cam, cam])
     oo, od, ot = O.raygen(cam)
@@ -458,8 +460,8 @@ def test_image_table_layout_matches_1d(medium):
 
 
 def test_mixed_cameras_one_launch(medium):
-    """Pinhole, fisheye, rolling-shutter and thin-lens views generated on the
-    GPU and rendered in one launch; per-ray results equal a 1-D launch, and
+    """Pinhole, fisheye, rolling-shutter, thin-lens and motion-blur views
+    generated on the GPU and rendered in one launch; per-ray results equal a 1-D launch, and
     the 4-sample thin-lens pixels average correctly."""
     sc, osc, o_, d_, cams = medium
     o0 = np.zeros(3)
@@ -467,9 +469,11 @@ def test_mixed_cameras_one_launch(medium):
           W.look_at_camera(1, 48, 32, W.orbit_eye(o0, 3.0, 100, 20), o0),
           W.look_at_camera(2, 48, 32, W.orbit_eye(o0, 3.0, 190, 20), o0, rs_velocity=(0.05, 0.0, 0.0)),
           W.look_at_camera(3, 48, 32, W.orbit_eye(o0, 3.0, 280, 20), o0, lens_radius=0.01, focus_dist=3.0,
-                           lens_samples=4, seed=7)]
+                           lens_samples=4, seed=7),
+          W.look_at_camera(4, 48, 32, W.orbit_eye(o0, 3.0, 330, 20), o0, rs_velocity=(0.0, 0.02, 0.01),
+                           lens_samples=2, seed=8)]
     o, d, t = api.generate_rays(mk)
-    sizes = [(48 * (4 if c.kind == 3 else 1), 32) for c in mk]
+    sizes = [(48 * c.spp, 32) for c in mk]
     base = W.default_params()
     scene = api.Scene.from_workload(sc)
     a = api.render_fwd(scene, o, d, gpu_params(base, image_sizes=sizes), time=t)
@@ -477,7 +481,7 @@ def test_mixed_cameras_one_launch(medium):
     assert scene.get_error()[0] == 0
     assert torch.equal(a[0], b[0]) and torch.equal(a[2], b[2])
     n_px = 48 * 32
-    lens = a[0][3 * n_px:]
+    lens = a[0][3 * n_px:7 * n_px]
     px = api.average_samples(lens.contiguous(), 4)
     assert torch.allclose(px, lens.view(n_px, 4, 3).mean(1), atol=1e-6)
 
@@ -515,3 +519,61 @@ def test_gradients_vs_finite_differences_on_surface_crop():
     for kind, idx, fd, an in res:
         v = got[kind][idx]
         assert abs(v - fd) <= GRAD_REL * max(abs(fd), floors[kind]), (kind, idx, v, fd)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_paper_appearance_model(medium, dtype):
+    """Appearance 1 (Sec. 5.1-5.2): c = sigmoid(T_vi(oct(surface direction)) +
+    T_vd(oct(-d))). Forward images and the gradients of sites, sigma and both
+    textures against the oracle; rays start in big empty cells, so the
+    exit-point rule of the origin cell is exercised too."""
+    sc, osc_, o, d, cams = medium
+    rng = np.random.default_rng(90)
+    tvi = rng.normal(0.0, 1.5, size=sc.tex.shape).astype(np.float32)
+    tvd = rng.normal(0.0, 0.5, size=sc.tex.shape).astype(np.float32)
+    if dtype == "f16":  # the oracle sees the stored (rounded) values
+        tvi_o, tvd_o = [torch.as_tensor(x).half().float().numpy() for x in (tvi, tvd)]
+    else:
+        tvi_o, tvd_o = tvi, tvd
+    base = W.default_params()
+    P = gpu_params(base, img_w=203, img_h=121, n_images=2, appearance=1)
+    scene = api.Scene(sc.sites, sc.sigma, tvi, sc.offsets, sc.indices, tex_dtype=dtype, tex_vd=tvd)
+    to, td = to_dev(o, d)
+    rgb, res = fwd_res(scene, to, td, P)
+    assert scene.get_error()[0] == 0
+    osc = O.OracleScene(sc.sites, sc.sigma, tvi_o, sc.offsets, sc.indices, tex_vd=tvd_o)
+    op = O.make_params(**base, appearance=1)
+    orgb, _, _, flags = O.render(osc, o, d, params=op)
+    ok = (flags & O.BAND_FLAGS) == 0
+    assert ok.mean() > 0.95
+    assert np.abs(rgb.cpu().numpy()[ok] - orgb[ok]).max() <= IMG_TOL
+    g = (rng.normal(size=(len(o), 3)) * ok[:, None]).astype(np.float32)
+    gvd = torch.empty(sc.n, sc.R, sc.R, 3, device=DEV)
+    gs, gsig, gt = api.render_bwd(scene, to, td, P, rgb, torch.as_tensor(g, device=DEV), residual=res,
+                                  tex_vd_out=gvd)
+    ogs, ogsig, ogt, ogvd = O.render_bwd(osc, o, d, g.astype(np.float64), params=op)
+    grad_close(gsig.cpu().numpy(), ogsig, "sigma")
+    grad_close(gt.cpu().numpy(), ogt, "tex_vi")
+    grad_close(gvd.cpu().numpy(), ogvd, "tex_vd")
+    grad_close(gs.cpu().numpy(), ogs, "sites")
+
+
+def test_paper_appearance_autograd_and_rejections(tiny):
+    wl, osc, o, d = tiny
+    sc = wl.scene
+    tvd = np.zeros_like(sc.tex)
+    scene = api.Scene.from_workload(sc, tex_vd=tvd)
+    P = gpu_params(wl.params, img_w=64, img_h=64, n_images=1, appearance=1)
+    sites = torch.tensor(sc.sites, device=DEV, requires_grad=True)
+    sigma = torch.tensor(sc.sigma, device=DEV, requires_grad=True)
+    tex = torch.tensor(sc.tex, device=DEV, requires_grad=True)
+    tex_vd = torch.tensor(tvd, device=DEV, requires_grad=True)
+    to, td = to_dev(o, d)
+    rgb = api.render(sites, sigma, tex, to, td, scene, P, tex_vd=tex_vd)
+    rgb.sum().backward()
+    assert tex_vd.grad is not None and torch.isfinite(tex_vd.grad).all()
+    assert (tex_vd.grad.abs().sum() > 0).item()
+    # appearance 1 needs a scene with a view-dependent texture
+    plain = api.Scene.from_workload(sc)
+    with pytest.raises(api._vt.VTError):
+        api.render_fwd(plain, to, td, P)

@@ -570,6 +570,60 @@ def test_thin_lens_focus():
         assert np.all(np.sign(ly[:, s_]) == (1 if sy else -1))
 
 
+def test_motion_blur_times_and_origins():
+    """Camera motion blur (Sec. 6.5): S time samples per pixel over the
+    exposure [0, 1), one per stratum, with the camera centre moved linearly
+    (eye + t * velocity) and the pinhole direction of that pixel."""
+    v = np.array([0.04, -0.01, 0.02])
+    S = 5
+    cam = W.look_at_camera(4, 14, 9, (0.0, -3.0, 0.0), (0.0, 0.0, 0.0), rs_velocity=tuple(v), lens_samples=S,
+                           seed=77)
+    assert cam.n_rays == 14 * 9 * S
+    o, d, t = O.raygen(cam)
+    assert o.shape == (14 * 9 * S, 3)
+    _, pin_d, _ = O.raygen(W.look_at_camera(0, 14, 9, (0.0, -3.0, 0.0), (0.0, 0.0, 0.0)))
+    assert np.allclose(d, np.repeat(pin_d, S, axis=0), atol=1e-15)
+    tt = t.reshape(-1, S)
+    strata = np.arange(S)[None, :]
+    assert np.all(tt >= strata / S) and np.all(tt < (strata + 1) / S)  # one sample per stratum
+    assert np.allclose(o, np.array(cam.eye) + t[:, None] * v, atol=1e-15)
+    # jitter: the SplitMix64 counter hash of (seed, pixel * S + s), even counters
+    pix = np.repeat(np.arange(14 * 9), S)
+    s_ = np.tile(np.arange(S), 14 * 9)
+    j = np.array([O.uniform(77, int((p_ * S + k) << 1)) for p_, k in zip(pix, s_)])
+    assert np.allclose(t, (s_ + j) / S, atol=1e-15)
+    # the offsets within the strata are uniform: mean 1/2, variance 1/12
+    u = tt * S - strata
+    assert abs(u.mean() - 0.5) < 0.05 and abs(u.var() - 1 / 12) < 0.02
+    # a resting camera reproduces the pinhole image sample by sample
+    still = O.raygen(W.look_at_camera(4, 14, 9, (0.0, -3.0, 0.0), (0.0, 0.0, 0.0), lens_samples=S, seed=77))
+    assert np.allclose(still[0], np.array(cam.eye)) and np.allclose(still[1], d)
+
+
+def test_motion_blur_render_is_time_average(tiny):
+    """The per-pixel mean of the motion-blur samples estimates the time
+    average of pinhole renders along the camera path: with many samples it
+    agrees with a fine Riemann sum over shifted pinhole cameras."""
+    wl, osc = tiny
+    p = O.make_params(**wl.params)
+    eye = np.array(W.orbit_eye(np.zeros(3), 2.2, 30.0, 15.0))
+    v = np.array([0.0, 0.0, 0.3])
+    S = 64
+    cam = W.look_at_camera(4, 6, 5, tuple(eye), (0.0, 0.0, 0.0), rs_velocity=tuple(v), lens_samples=S, seed=5)
+    o, d, _ = O.raygen(cam)
+    rgb, _, _, _ = O.render(osc, o, d, params=p)
+    blur = rgb.reshape(30, S, 3).mean(1)
+    M = 256
+    acc = np.zeros((30, 3))
+    for k in range(M):
+        e = eye + (k + 0.5) / M * v
+        po, pd, _ = O.raygen(W.look_at_camera(0, 6, 5, tuple(e), tuple(e - eye), fov_y=cam.fov_y))
+        acc += O.render(osc, po, pd, params=p)[0]
+    acc /= M
+    # stratified estimate of a piecewise-smooth integrand: error well below 1e-2
+    assert np.abs(blur - acc).max() < 3e-2 and np.abs(blur - acc).mean() < 5e-3
+
+
 # ---------------------------------------------------------------- the 1,000-site crop (surface distribution)
 
 def crop_setup():
@@ -646,3 +700,319 @@ def test_fd_on_surface_crop():
     assert kinds.count("sites") >= 15 and kinds.count("sigma") == 20 and kinds.count("tex") == 20
     for kind, idx, fd, an in res:
         assert abs(fd - an) <= 1e-4 * max(abs(an), floors[kind]), (kind, idx, fd, an)
+
+
+# ---------------------------------------------------------------- appearance model of Sec. 5.1-5.2
+
+def _sigmoid(z):
+    return 1.0 / (1.0 + np.exp(-z))
+
+
+def test_paper_appearance_closed_form_single_cell():
+    a = np.array([0.3, -1.2, 2.0])
+    b = np.array([-0.5, 0.4, 0.1])
+    tex = np.broadcast_to(a, (1, 4, 4, 3)).copy()
+    tvd = np.broadcast_to(b, (1, 4, 4, 3)).copy()
+    sc = O.OracleScene([[0.1, 0.2, 0.3]], [1.3], tex, [0, 0], np.zeros(0, np.int32), tex_vd=tvd)
+    bg = np.array([1.0, 0.9, 0.8])
+    for _ in range(10):
+        o = RNG.uniform(-1, 1, size=3)
+        d = RNG.normal(size=3)
+        d /= np.linalg.norm(d)
+        rgb, T, _, _ = O.render(sc, o[None], d[None], t_far=2.0, T_eps=0.0, bg=bg, appearance=1)
+        L = 2.0
+        assert np.allclose(rgb[0], (1 - np.exp(-1.3 * L)) * _sigmoid(a + b) + np.exp(-1.3 * L) * bg, atol=1e-14)
+
+
+def test_paper_appearance_surface_directions():
+    """Two cells: the origin cell is coloured at its exit point, the next cell at
+    its entry point -- the same bisector crossing x*. Textures linear in texel
+    coordinates make the colour a closed form of oct((x* - s)/|x* - s|)."""
+    R = 8
+    s1, s2 = np.array([0.0, 0.0, 0.0]), np.array([1.0, 0.3, -0.2])
+    A = [np.array([0.1, -0.2, 0.3]), np.array([-0.4, 0.2, 0.0])]
+    Bx = [np.array([0.05, -0.1, 0.2]), np.array([0.3, 0.05, -0.07])]
+    By = [np.array([-0.2, 0.15, 0.02]), np.array([0.01, -0.3, 0.11])]
+    ys, xs = np.meshgrid(np.arange(R), np.arange(R), indexing="ij")
+    tex = np.stack([A[k] + Bx[k] * xs[..., None] + By[k] * ys[..., None] for k in range(2)])
+    tvd = np.zeros_like(tex)
+    sc = O.OracleScene(np.stack([s1, s2]), [0.7, 3.0], tex, [0, 1, 2], np.array([1, 0], np.int32), tex_vd=tvd)
+    o = np.array([-0.6, 0.05, 0.02])
+    d = np.array([1.0, 0.12, -0.05])
+    d /= np.linalg.norm(d)
+    tstar = np.dot(s2 - s1, 0.5 * (s1 + s2) - o) / np.dot(s2 - s1, d)
+    x = o + tstar * d
+    cols = []
+    for k, s in enumerate((s1, s2)):
+        u, v = _oct_from_geometry((x - s) / np.linalg.norm(x - s))
+        xt = min(max((u + 1) / 2 * R - 0.5, 0), R - 1)
+        yt = min(max((v + 1) / 2 * R - 0.5, 0), R - 1)
+        cols.append(_sigmoid(A[k] + Bx[k] * xt + By[k] * yt))
+    t_far = 3.0
+    rgb, _, _, _ = O.render(sc, o[None], d[None], t_far=t_far, T_eps=0.0, bg=(0, 0, 0), appearance=1)
+    a1 = 1 - np.exp(-0.7 * tstar)
+    a2 = 1 - np.exp(-3.0 * (t_far - tstar))
+    assert np.allclose(rgb[0], a1 * cols[0] + (1 - a1) * a2 * cols[1], atol=1e-13)
+
+
+def test_fd_paper_appearance_on_surface_crop():
+    sc, o, d, Y, params = crop_setup()
+    rng = np.random.default_rng(21)
+    tex_vi = rng.normal(0.0, 1.5, size=sc.tex.shape)
+    tex_vd = rng.normal(0.0, 0.5, size=sc.tex.shape)
+    params = dict(params, appearance=1)
+    p = O.make_params(**params)
+    osc = O.OracleScene(sc.sites, sc.sigma, tex_vi, sc.offsets, sc.indices, tex_vd=tex_vd)
+    s64, sig64 = osc.sites, osc.sigma
+    rgb = O.render(osc, o, d, params=p, n_threads=1)[0]
+    gs, gsig, gt, gtv = O.render_bwd(osc, o, d, rgb - Y, params=p)
+    base_cells = O.trace(osc, o, d, params=p, n_threads=1)[0]
+
+    def L(sites=s64, sigma=sig64, tvi=tex_vi, tvd=tex_vd):
+        sc2 = O.OracleScene(sites, sigma, tvi, sc.offsets, sc.indices, tex_vd=tvd)
+        return 0.5 * np.sum((O.render(sc2, o, d, params=p, n_threads=1)[0] - Y) ** 2), sc2
+
+    def check(fd, an, scale):
+        assert abs(fd - an) <= 1e-4 * max(abs(an), 1e-3 * scale), (fd, an)
+
+    for arr, g, name in ((tex_vi, gt, "vi"), (tex_vd, gtv, "vd")):
+        cand = np.argwhere(np.abs(g) > 1e-9)
+        for q in cand[rng.choice(len(cand), size=10, replace=False)]:
+            v = []
+            for sgn in (1, -1):
+                a2 = arr.copy()
+                a2[tuple(q)] += sgn * 1e-5
+                v.append(L(**({"tvi": a2} if name == "vi" else {"tvd": a2}))[0])
+            check((v[0] - v[1]) / 2e-5, g[tuple(q)], np.abs(g).max())
+    for i in rng.choice(np.nonzero(np.abs(gsig) > 1e-9)[0], size=10, replace=False):
+        h = 1e-6 * max(1.0, sig64[i])
+        v = []
+        for sgn in (1, -1):
+            sg = sig64.copy()
+            sg[i] += sgn * h
+            v.append(L(sigma=sg)[0])
+        check((v[0] - v[1]) / (2 * h), gsig[i], np.abs(gsig).max())
+    cand = np.argwhere(np.abs(gs) > 1e-7)
+    n = 0
+    for q in cand[rng.permutation(len(cand))]:
+        v = []
+        for sgn in (1, -1):
+            ss = s64.copy()
+            ss[q[0], q[1]] += sgn * 1e-7
+            val, sc2 = L(sites=ss)
+            if not np.array_equal(O.trace(sc2, o, d, params=p, n_threads=1)[0], base_cells):
+                v = None
+                break
+            v.append(val)
+        if v is None:
+            continue
+        check((v[0] - v[1]) / 2e-7, gs[tuple(q)], np.abs(gs).max())
+        n += 1
+        if n >= 20:
+            break
+    assert n >= 15
+
+
+def test_fd_paper_appearance_rays_starting_inside():
+    """Origins inside the crop: the cell holding the origin is composited and
+    coloured at its exit point, so its site and exit crossing get gradients."""
+    sc, o_out, d_out, Y, params = crop_setup()
+    rng = np.random.default_rng(22)
+    lo, hi = np.array(params["clip_lo"]), np.array(params["clip_hi"])
+    c = 0.5 * (lo + hi)
+    n = 400
+    o = c + rng.uniform(-0.05, 0.05, size=(n, 3))
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    Y = rng.uniform(0, 1, size=(n, 3))
+    tex_vi = rng.normal(0.0, 1.5, size=sc.tex.shape)
+    tex_vd = rng.normal(0.0, 0.5, size=sc.tex.shape)
+    p = O.make_params(**dict(params, appearance=1))
+    osc = O.OracleScene(sc.sites, sc.sigma, tex_vi, sc.offsets, sc.indices, tex_vd=tex_vd)
+    rgb = O.render(osc, o, d, params=p, n_threads=1)[0]
+    gs = O.render_bwd(osc, o, d, rgb - Y, params=p)[0]
+    base_cells = O.trace(osc, o, d, params=p, n_threads=1)[0]
+    first = set(base_cells[:, 0].tolist())  # origin cells
+    checked = 0
+    for i in rng.permutation(sorted(first)):
+        for k in range(3):
+            if abs(gs[i, k]) < 1e-7:
+                continue
+            v = []
+            for sgn in (1, -1):
+                ss = osc.sites.copy()
+                ss[i, k] += sgn * 1e-7
+                sc2 = O.OracleScene(ss, osc.sigma, tex_vi, sc.offsets, sc.indices, tex_vd=tex_vd)
+                if not np.array_equal(O.trace(sc2, o, d, params=p, n_threads=1)[0], base_cells):
+                    v = None
+                    break
+                v.append(0.5 * np.sum((O.render(sc2, o, d, params=p, n_threads=1)[0] - Y) ** 2))
+            if v is None:
+                continue
+            fd = (v[0] - v[1]) / 2e-7
+            assert abs(fd - gs[i, k]) <= 1e-4 * max(abs(gs[i, k]), 1e-3 * np.abs(gs).max()), (i, k, fd, gs[i, k])
+            checked += 1
+        if checked >= 12:
+            break
+    assert checked >= 8
+
+
+# ---------------------------------------------------------------- distortion loss (Eq. 2) and sigma = exp(rho)
+
+def _s(t):
+    return 1.0 - 1.0 / (1.0 + t)
+
+
+def test_distortion_single_cell_closed_form():
+    # one cell over [t_near, t_far]: only the self term, w^2 (s(b) - s(a)) / 3
+    sc = _one_site_scene([0.1, 0.2, 0.3], 1.3, [0.5, 0.5, 0.5])
+    for _ in range(10):
+        o = RNG.uniform(-2, 2, size=3)
+        d = RNG.normal(size=3)
+        d /= np.linalg.norm(d)
+        a, b = 0.2, RNG.uniform(0.5, 3)
+        L = O.distortion(sc, o[None], d[None], t_near=a, t_far=b, T_eps=0.0)
+        w = 1 - math.exp(-1.3 * (b - a))
+        assert abs(L[0] - w * w * (_s(b) - _s(a)) / 3) < 1e-15
+
+
+def test_distortion_two_cells_closed_form():
+    s1, s2 = np.array([0.0, 0.0, 0.0]), np.array([1.0, 0.2, -0.1])
+    tex = np.full((2, 4, 4, 3), 0.5)
+    sc = O.OracleScene(np.stack([s1, s2]), [0.9, 2.5], tex, [0, 1, 2], np.array([1, 0], np.int32))
+    o = np.array([-1.0, 0.05, 0.02])
+    d = np.array([1.0, 0.1, 0.0])
+    d /= np.linalg.norm(d)
+    tstar = np.dot(s2 - s1, 0.5 * (s1 + s2) - o) / np.dot(s2 - s1, d)
+    L = O.distortion(sc, o[None], d[None], t_far=4.0, T_eps=0.0)[0]
+    w1 = 1 - math.exp(-0.9 * tstar)
+    w2 = (1 - w1) * (1 - math.exp(-2.5 * (4.0 - tstar)))
+    m1, m2 = 0.5 * (_s(0) + _s(tstar)), 0.5 * (_s(tstar) + _s(4.0))
+    # ordered pairs (1,2) and (2,1), then the two self terms
+    ex = 2 * w1 * w2 * (m2 - m1) + (w1 ** 2 * (_s(tstar) - _s(0)) + w2 ** 2 * (_s(4.0) - _s(tstar))) / 3
+    assert abs(L - ex) < 1e-15
+
+
+def test_distortion_is_double_integral_of_weight_histogram(tiny):
+    """Mip-NeRF 360: the loss equals the double integral of |u - v| against
+    the step-function weight density (w_k spread uniformly over
+    [s(a_k), s(b_k)]). Midpoint quadrature with m points per interval has
+    relative error 1/m^2 on the self terms."""
+    wl, osc = tiny
+    p = O.make_params(**wl.params)
+    o, d = W.workload_rays(wl)
+    rng = np.random.default_rng(8)
+    L = O.distortion(osc, o, d, params=p)
+    checked = 0
+    m = 400
+    for r in rng.permutation(len(o)):
+        sg = O.segments(osc, o[r], d[r], params=p)
+        sel = sg["composited"] == 1
+        if sel.sum() < 3:
+            continue
+        a, b = sg["a"][sel], sg["b"][sel]
+        w = sg["T_before"][sel] * sg["alpha"][sel]
+        lo, hi = _s(a), _s(b)
+        x = (np.arange(m) + 0.5) / m
+        u = (lo[:, None] + x[None, :] * (hi - lo)[:, None]).ravel()
+        wu = np.repeat(w / m, m)
+        I = 0.0
+        for c in range(0, len(u), 2000):
+            I += np.sum(wu[c:c + 2000, None] * wu[None, :] * np.abs(u[c:c + 2000, None] - u[None, :]))
+        assert abs(I - L[r]) <= 2e-5 * L[r] + 1e-15, (r, I, L[r])
+        checked += 1
+        if checked >= 8:
+            break
+    assert checked == 8
+
+
+def _crop_dist_fd(params, n_each=15, seed=4):
+    """Central differences of sum_r gd_r L_dist(r) on the 1,000-site crop
+    against the oracle's adjoint (grad_rgb = 0)."""
+    sc, o, d, _, _ = crop_setup()
+    p = O.make_params(**params)
+    osc = O.OracleScene.from_workload_scene(sc)
+    gd = np.random.default_rng(11).uniform(0.5, 1.5, size=len(o))
+    gs, gsig, gt = O.render_bwd(osc, o, d, np.zeros((len(o), 3)), params=p, grad_dist=gd)
+    assert np.all(gt == 0)
+    s64, sig64 = osc.sites, osc.sigma
+    base_cells = O.trace(osc, o, d, params=p, n_threads=1)[0]
+
+    def F(sites=s64, sigma=sig64):
+        sc2 = O.OracleScene(sites, sigma, osc.tex, sc.offsets, sc.indices)
+        return float(gd @ O.distortion(sc2, o, d, params=p, n_threads=1)), sc2
+
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in rng.choice(np.nonzero(np.abs(gsig) > 1e-9)[0], size=n_each, replace=False):
+        h = 1e-6 * max(1.0, sig64[i])
+        v = []
+        for sgn in (1, -1):
+            sg = sig64.copy()
+            sg[i] += sgn * h
+            v.append(F(sigma=sg)[0])
+        out.append(("sigma", (v[0] - v[1]) / (2 * h), gsig[i], np.abs(gsig).max()))
+    cand = np.argwhere(np.abs(gs) > 1e-9)
+    n_sites = 0
+    for q in cand[rng.permutation(len(cand))]:
+        i, c = int(q[0]), int(q[1])
+        h = 1e-7
+        v = []
+        for sgn in (1, -1):
+            ss = s64.copy()
+            ss[i, c] += sgn * h
+            val, sc2 = F(sites=ss)
+            if not np.array_equal(O.trace(sc2, o, d, params=p, n_threads=1)[0], base_cells):
+                break
+            v.append(val)
+        if len(v) < 2:
+            continue
+        out.append(("sites", (v[0] - v[1]) / (2 * h), gs[i, c], np.abs(gs).max()))
+        n_sites += 1
+        if n_sites >= n_each:
+            break
+    return out
+
+
+def test_fd_distortion_on_surface_crop():
+    sc, o, d, Y, params = crop_setup()
+    res = _crop_dist_fd(params)
+    assert sum(r[0] == "sites" for r in res) >= 10
+    for kind, fd, an, mx in res:
+        assert abs(fd - an) <= 1e-4 * max(abs(an), 1e-3 * mx), (kind, fd, an)
+
+
+def test_distortion_gradient_adds_to_colour_gradient(tiny):
+    # the adjoint is linear in (dL/dC, dL/dL_dist)
+    wl, osc = tiny
+    p = O.make_params(**wl.params)
+    o, d = W.workload_rays(wl)
+    o, d = o[:600], d[:600]
+    rng = np.random.default_rng(3)
+    g = rng.normal(size=(len(o), 3))
+    gd = rng.uniform(0, 1, size=len(o))
+    a = O.render_bwd(osc, o, d, g, params=p)
+    b = O.render_bwd(osc, o, d, np.zeros_like(g), params=p, grad_dist=gd)
+    c = O.render_bwd(osc, o, d, g, params=p, grad_dist=gd)
+    for x, y, z in zip(a, b, c):
+        assert np.allclose(x + y, z, rtol=1e-12, atol=1e-12 * max(1.0, np.abs(z).max()))
+
+
+def test_exp_density_gradient_is_size_invariant():
+    """Eq. 4: with sigma = exp(rho), dL/drho = dL/dalpha (1 - alpha) ln(1/(1 - alpha)):
+    two single-cell rays of equal opacity but segment lengths 0.1 and 2.0
+    give the same dL/drho; dL/dsigma differs by the length ratio (Eq. 3)."""
+    c, bg = np.array([0.9, 0.1, 0.4]), np.array([0.0, 0.0, 0.0])
+    g = np.array([0.5, -0.2, 0.3])
+    alpha = 0.6
+    out = []
+    for L in (0.1, 2.0):
+        rho = math.log(-math.log(1 - alpha) / L)
+        sigma = O.density_from_log([rho])
+        sc = _one_site_scene([0, 0, 0], sigma[0], c)
+        _, gsig, _ = O.render_bwd(sc, np.zeros((1, 3)), np.array([[0, 0, 1.0]]), g[None], t_far=L, T_eps=0.0, bg=bg)
+        grho = O.density_log_bwd(sigma, gsig)[0]
+        out.append((gsig[0], grho))
+        assert abs(grho - (g @ (c - bg)) * (1 - alpha) * math.log(1 / (1 - alpha))) < 1e-14
+    assert abs(out[0][1] - out[1][1]) < 1e-14
+    assert abs(out[0][0] / out[1][0] - 0.1 / 2.0) < 1e-12
