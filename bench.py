@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the FP32/BF16 comparison timings")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--skip-sweep", action="store_true",
+                    help="forward-only timing and image change for cell-skip thresholds 0 ... 1e-2")
     ap.add_argument("--ablation", action="store_true",
                     help="also time the forward pass with the inference-stack toggles (Morton order, 4x8 tiles, "
                          "cell skip 1e-3), cumulatively as in the paper's Sec. 6.3 ablation")
@@ -283,6 +285,72 @@ def run_ours(args, ws, rank, local):
                                 "ms_fwd": round(m_f, 3), "ms_bwd": round(m_b, 3), "tex": args.tex}
         params = params_main
         sc_app.close()
+        # inference with FP16 neighbour offsets (Sec. 5.6): forward only
+        sc_h = api.Scene.from_workload(wl.scene, tex_dtype=args.tex, device=dev, half_offsets=True)
+        api.generate_rays(cams, out=(o, d, tm))
+        api.render_fwd(main, o, d, params, time=tm, out=(rgb, T, steps))
+        ref_img = rgb.clone()
+        ms_h, _, _ = timed(sc_h, max(3, args.steps // 2), fwd_only=True)
+        mse = ((rgb.double() - ref_img.double()) ** 2).mean().item()
+        extra["half_offsets_fwd"] = {"fwd_only_mrays_s": round(n_rays / (ms_h * 1e-3) / 1e6 * ws, 2),
+                                     "psnr_vs_fp32_offsets_db": None if mse == 0 else round(-10 * math.log10(mse), 2),
+                                     "max_abs_diff": round((rgb - ref_img).abs().max().item(), 6)}
+        sc_h.close()
+        del ref_img
+        # training step with the distortion loss (Eq. 2) fused into both passes
+        dist = torch.empty(n_rays, 3, device=dev)
+        gdist = torch.full((n_rays,), 1e-2 / n_rays, device=dev)
+
+        def step_dist():
+            api.generate_rays(cams, out=(o, d, tm))
+            api.render_fwd(main, o, d, params, time=tm, out=(rgb, T, steps), residual=res, dist=dist)
+            loss, grad = api.l2_loss(rgb, Y)
+            api.render_bwd(main, o, d, params, rgb, grad, time=tm, out=(gs, gsig, gt), residual=res, dist=dist,
+                           grad_dist=gdist)
+
+        for _ in range(args.warmup):
+            step_dist()
+        barrier()
+        reps, tot = max(3, args.steps // 2), 0.0
+        for _ in range(reps):
+            flush.zero_()
+            a, b = ev(), ev()
+            a.record(stream)
+            step_dist()
+            b.record(stream)
+            barrier()
+            tot += a.elapsed_time(b)
+        extra["distortion_loss"] = {"fwd_bwd_mrays_s": round(n_rays / (tot / reps * 1e-3) / 1e6 * ws, 2),
+                                    "mean_L_dist": round(dist[:, 0].double().mean().item(), 6)}
+        del dist, gdist
+        # one optimisation iteration of the training loop (Eq. 5 with the paper's
+        # appearance model, distortion loss, regularisers, Adam; no Delaunay refresh)
+        from paper_2608_17682_gb300 import train as TRN
+
+        rng = np.random.default_rng(6000 + wl.seed)
+        cfg = TRN.TrainConfig(iters=1000, rays_per_iter=1 << 20, refresh_every=0)
+        tr = TRN.Trainer(wl.scene.sites, np.log(np.maximum(wl.scene.sigma, 1e-6)),
+                         rng.normal(0.0, 1.0, size=wl.scene.tex.shape).astype(np.float32),
+                         np.zeros(wl.scene.tex.shape, np.float32), cams, Y, dict(wl.params), cfg, device=dev,
+                         offsets=wl.scene.offsets, indices=wl.scene.indices)
+        for _ in range(args.warmup):
+            tr.step()
+        barrier()
+        reps = max(3, args.steps // 2)
+        a, b = ev(), ev()
+        a.record(stream)
+        for _ in range(reps):
+            tr.step()
+        b.record(stream)
+        barrier()
+        ms_it = a.elapsed_time(b) / reps
+        st_, _ = tr.scene.get_error()
+        extra["train_iteration"] = {"rays_per_iter": tr.B, "ms_per_iter": round(ms_it, 3),
+                                    "mrays_s": round(tr.B / (ms_it * 1e-3) / 1e6, 2), "kernel_status": st_,
+                                    "note": "sigma=exp(rho), sampling, fwd+bwd (appearance 1, distortion), "
+                                            "Smooth-L1, regularisers, 4 Adam updates; L2 not flushed"}
+        tr.scene.close()
+        del tr
 
     if args.ablation:
         # cumulative: user order + row-major 1-D rays -> + Morton -> + 4x8 tiles -> + skip 1e-3
@@ -310,6 +378,39 @@ def run_ours(args, ws, rank, local):
                          "fps": round(n_img / (ms * 1e-3), 1)})
         extra["ablation_fwd"] = rows
         del base_scene
+
+    if args.skip_sweep:
+        # inference speed / quality trade-off of the low-contribution cell skip
+        # (Sec. 5.6): PSNR of each image against the unskipped render
+        rows = []
+        exact = None
+        for thr in (0.0, 1e-5, 1e-4, 3e-4, 1e-3, 3e-3, 1e-2):
+            pp = api.make_params(**{**wl.params, "skip_weight": thr}, **layout)
+            for _ in range(args.warmup):
+                api.generate_rays(cams, out=(o, d, tm))
+                api.render_fwd(main, o, d, pp, time=tm, out=(rgb, T, steps))
+            barrier()
+            tot = 0.0
+            reps = max(3, args.steps // 2)
+            for _ in range(reps):
+                flush.zero_()
+                a, b = ev(), ev()
+                a.record(stream)
+                api.render_fwd(main, o, d, pp, time=tm, out=(rgb, T, steps))
+                b.record(stream)
+                barrier()
+                tot += a.elapsed_time(b)
+            ms = tot / reps
+            img = rgb.double()
+            if exact is None:
+                exact = img.clone()
+            mse = ((img - exact) ** 2).mean().item()
+            psnr = None if mse == 0 else round(10 * math.log10(1.0 / mse), 2)
+            rows.append({"threshold": thr, "ms_fwd": round(ms, 3), "fps": round(n_img / (ms * 1e-3), 1),
+                         "mrays_s": round(n_rays / (ms * 1e-3) / 1e6, 1), "psnr_vs_unskipped_db": psnr,
+                         "max_abs_diff": round((img - exact).abs().max().item(), 6)})
+        extra["skip_sweep_fwd"] = rows
+        del exact
 
     # end to end through the public API with host buffers: H2D target image,
     # D2H rendered image + loss, inside the timed region

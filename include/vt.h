@@ -75,12 +75,23 @@ typedef struct {
                                   no duplicates within a row, E < 2^31; may be
                                   NULL when E == 0                                 */
   int32_t flags;               /* VT_SCENE_KEEP_ORDER: store cells in user order
-                                  instead of Morton order (for ablations)         */
+                                  instead of Morton order (for ablations);
+                                  VT_SCENE_HALF_OFFSETS: see below                */
   const float* tex_vd;         /* optional [N,R,R,3] view-dependent texture T_vd
                                   (Sec. 5.2), logits; required for appearance 1   */
 } vt_scene_desc;
 
 #define VT_SCENE_KEEP_ORDER 1
+/* VT_SCENE_HALF_OFFSETS: also store each neighbour offset s_j - s_i as three
+ * FP16 values (8-byte records, Sec. 5.6: the inference kernel's
+ * half-precision neighbour vectors) and let vt_render_fwd / vt_trace_cells
+ * search exits with them. The planes then pass through s_i + n_h/2 with
+ * normal n_h = fp16(s_j - s_i), not exactly through the bisector, so cell
+ * sequences can differ from the exact walk near Voronoi edges. Forward
+ * only: vt_render_bwd, vt_render_bwd_static and the distortion output return
+ * VT_ERR_UNSUPPORTED on such a scene. Offsets must be below 65504 in
+ * magnitude (VT_ERR_INVALID_ARG otherwise). */
+#define VT_SCENE_HALF_OFFSETS 2
 
 /* Render parameters. Rays are r(t) = o + t d for t in [t_near, t_far],
  * optionally clipped to the box [clip_lo, clip_hi]. */
@@ -212,13 +223,23 @@ vt_status vt_generate_rays(const vt_camera* cams, int32_t n_cams, float* o, floa
  *   rgb_residual: DEVICE [n_rays,3] or NULL: the rounding residual C - rgb_out
  *            of the float-float colour. Passing it to vt_render_bwd lets the
  *            backward form the suffix sums C - sum_{m<=k} w_m c_m without the
- *            FP32 rounding of C (which limits deep-ray gradients to ~1e-3). 
+ *            FP32 rounding of C (which limits deep-ray gradients to ~1e-3).
+ *   dist_out: DEVICE [n_rays,3] or NULL: the distortion loss of Mip-NeRF 360
+ *            (Sec. 5.3, Eq. 2) of each ray, computed in the same pass:
+ *              dist_out[3r]   = L_dist(r) = sum_{k,l} w_k w_l |sbar_k - sbar_l|
+ *                                           + 1/3 sum_k w_k^2 ds_k,
+ *            w_k = T_k alpha_k over the composited intervals [a_k, b_k],
+ *            s(t) = 1 - 1/(1+t) of the ray parameter t, sbar_k = (s(a_k) +
+ *            s(b_k))/2, ds_k = s(b_k) - s(a_k);
+ *              dist_out[3r+1] = sum_k w_k, dist_out[3r+2] = sum_k w_k (sbar_k -
+ *            sbar_first): totals that vt_render_bwd reads back. Requires
+ *            t_near >= 0 (VT_ERR_INVALID_ARG otherwise).
  * The start cell of each ray is found by an exact nearest-site search for one
  * anchor origin per image (per 4096 rays in 1-D layout) followed by a greedy
  * walk over the Delaunay graph to the ray's own origin. */
 vt_status vt_render_fwd(vt_scene* s, int64_t n_rays, const float* o, const float* d, const float* time,
                         const vt_render_params* p, float* rgb_out, float* T_out, int32_t* steps_out,
-                        float* rgb_residual, void* stream);
+                        float* rgb_residual, float* dist_out, void* stream);
 
 /* Backward render: re-traverses every ray with decisions identical to
  * vt_render_fwd (no per-ray cell lists are stored) and accumulates
@@ -227,17 +248,21 @@ vt_status vt_render_fwd(vt_scene* s, int64_t n_rays, const float* o, const float
  *   grad_tex   [N,R,R,3] (bilinear weights * T alpha * dL/dC),
  * all DEVICE FP32 in USER index order, OVERWRITTEN (the call zero-fills them).
  * rgb_out is the forward's output for the same rays and parameters and
- * rgb_residual (NULL allowed) its residual output; grad_rgb is dL/dC [n_rays,3]. Any of the three gradient pointers may be
- * NULL to skip that output. Library-owned scratch (one float4 per cell and
- * per texel) is allocated on first use and kept with the scene. */
+ * rgb_residual (NULL allowed) its residual output; grad_rgb is dL/dC [n_rays,3].
+ * grad_dist (DEVICE [n_rays] or NULL) is dL/dL_dist per ray; when given, the
+ * gradients include the distortion loss and dist_out must be the forward's
+ * dist_out for the same rays (VT_ERR_INVALID_ARG if NULL). Any of the gradient
+ * pointers may be NULL to skip that output; grad_tex_vd is for appearance 1.
+ * Library-owned scratch (one float4 per cell and per texel) is allocated on
+ * first use and kept with the scene. */
 vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float* d, const float* time,
                         const vt_render_params* p, const float* rgb_out, const float* rgb_residual,
-                        const float* grad_rgb, float* grad_sites, float* grad_sigma, float* grad_tex,
-                        float* grad_tex_vd, void* stream);
+                        const float* dist_out, const float* grad_rgb, const float* grad_dist, float* grad_sites,
+                        float* grad_sigma, float* grad_tex, float* grad_tex_vd, void* stream);
 
 /* Allocation-free backward (no counterpart in the paper). Same arguments,
- * outputs and numerics as vt_render_bwd without a colour residual, appearance
- * 0 only (appearance 1 returns VT_ERR_UNSUPPORTED), for callers that may not allocate
+ * outputs and numerics as vt_render_bwd without a colour residual or distortion
+ * loss, appearance 0 only (appearance 1 returns VT_ERR_UNSUPPORTED), for callers that may not allocate
  * device memory at the time of the call: vt_render_bwd allocates its gradient
  * scratch with cudaMalloc on its first call for a scene, and cudaMalloc can
  * synchronise the device and bypasses an application's own memory pool or
@@ -279,6 +304,48 @@ vt_status vt_average_samples(int64_t n_pixels, int32_t spp, const float* rgb_ray
                              void* stream);
 vt_status vt_average_samples_bwd(int64_t n_pixels, int32_t spp, const float* grad_px, float* grad_rays,
                                  void* stream);
+
+/* Scale-invariant density parameterisation (Sec. 5.4): sigma = exp(rho), and
+ * its adjoint grad_rho = grad_sigma * sigma (Eq. 4). DEVICE [n] FP32 arrays;
+ * the output may alias the input. */
+vt_status vt_sigma_from_rho(int64_t n, const float* rho, float* sigma, void* stream);
+vt_status vt_sigma_from_rho_bwd(int64_t n, const float* sigma, const float* grad_sigma, float* grad_rho,
+                                void* stream);
+
+/* ---- training step helpers (Sec. 5.5, Eq. 5, and the appendix's training
+ * settings). All pointers DEVICE, FP32, caller-owned. */
+
+/* Stratified ray sampling: from a pool of n_pool rays (o_pool, d_pool
+ * [n_pool,3], optional colours y_pool [n_pool,3]) draw n <= n_pool rays, one
+ * uniformly inside each stratum [k n_pool/n, (k+1) n_pool/n) (SplitMix64
+ * counter hash of (seed, k)), and gather them into o, d, y [n,3] (y NULL to
+ * skip) and their pool indices idx_out [n] (NULL allowed). The indices are
+ * increasing, so rays of one camera stay together; every pool ray is drawn
+ * with probability n/n_pool. */
+vt_status vt_sample_rays(int64_t n_pool, const float* o_pool, const float* d_pool, const float* y_pool, int64_t n,
+                         uint64_t seed, float* o, float* d, float* y, int64_t* idx_out, void* stream);
+
+/* Smooth-L1 photometric loss (L_rgb of Eq. 5): mean over the 3n channels of
+ * 0.5 r^2/beta (|r| < beta) else |r| - 0.5 beta, r = rgb - target; grad_out
+ * [n,3] (NULL allowed) receives dL/drgb, loss_out one float (overwritten). */
+vt_status vt_smooth_l1_loss(int64_t n, const float* rgb, const float* target, float beta, float* grad_out,
+                            float* loss_out, void* stream);
+
+/* Texture regularisers of Eq. 5 on [n_cells, R, R, 3] maps:
+ *   L_vd   = 1/(N R^2) sum_i |T_i^vd|^2,
+ *   L_mean = 1/(N R^2) sum_{i,u} |T_{i,u}^vi - 1/R^2 sum_v T_{i,v}^vi|^2;
+ * loss_out = lambda_vd L_vd + lambda_mean L_mean (overwritten); the weighted
+ * gradients are ADDED to grad_tex / grad_tex_vd (NULL to skip). */
+vt_status vt_texture_regularizers(int64_t n_cells, int32_t tex_res, const float* tex, const float* tex_vd,
+                                  float lambda_vd, float lambda_mean, float* grad_tex, float* grad_tex_vd,
+                                  float* loss_out, void* stream);
+
+/* One Adam step (Kingma & Ba) with bias correction at step >= 1:
+ *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
+ *   param -= lr (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps).
+ * param, m, v updated in place. */
+vt_status vt_adam_step(int64_t n, float* param, const float* grad, float* m, float* v, float lr, float beta1,
+                       float beta2, float eps, int64_t step, void* stream);
 
 /* Human-readable status name (static string). */
 const char* vt_status_str(vt_status s);

@@ -21,7 +21,9 @@ VT_CAM_PINHOLE, VT_CAM_FISHEYE_EQUIDIST, VT_CAM_ROLLING_SHUTTER, VT_CAM_THIN_LEN
 # every symbol include/vt.h declares
 EXPORTS = ["vt_render_params_default", "vt_scene_create", "vt_scene_update", "vt_scene_destroy", "vt_scene_info",
            "vt_scene_get_error", "vt_camera_n_rays", "vt_generate_rays", "vt_render_fwd", "vt_render_bwd",
-           "vt_render_bwd_static", "vt_trace_cells", "vt_l2_loss", "vt_average_samples", "vt_average_samples_bwd", "vt_status_str"]
+           "vt_render_bwd_static", "vt_trace_cells", "vt_l2_loss", "vt_average_samples", "vt_average_samples_bwd", "vt_sigma_from_rho",
+           "vt_sigma_from_rho_bwd", "vt_sample_rays", "vt_smooth_l1_loss", "vt_texture_regularizers", "vt_adam_step",
+           "vt_status_str"]
 
 
 class VTError(RuntimeError):
@@ -37,6 +39,7 @@ class vt_scene_desc(C.Structure):
 
 
 VT_SCENE_KEEP_ORDER = 1
+VT_SCENE_HALF_OFFSETS = 2
 
 
 class vt_render_params(C.Structure):
@@ -69,13 +72,19 @@ def _load():
         "vt_scene_get_error": ([P, P, P], C.c_int),
         "vt_camera_n_rays": ([P], I64),
         "vt_generate_rays": ([P, I32, P, P, P, P], C.c_int),
-        "vt_render_fwd": ([P, I64, P, P, P, P, P, P, P, P, P], C.c_int),
-        "vt_render_bwd": ([P, I64, P, P, P, P, P, P, P, P, P, P, P, P], C.c_int),
+        "vt_render_fwd": ([P, I64, P, P, P, P, P, P, P, P, P, P], C.c_int),
+        "vt_render_bwd": ([P, I64, P, P, P, P, P, P, P, P, P, P, P, P, P, P], C.c_int),
         "vt_render_bwd_static": ([P, I64, P, P, P, P, P, P, P, P, P, P], C.c_int),
         "vt_trace_cells": ([P, I64, P, P, P, I32, P, P, P, P], C.c_int),
         "vt_l2_loss": ([I64, P, P, P, P, P], C.c_int),
         "vt_average_samples": ([I64, I32, P, P, P], C.c_int),
         "vt_average_samples_bwd": ([I64, I32, P, P, P], C.c_int),
+        "vt_sigma_from_rho": ([I64, P, P, P], C.c_int),
+        "vt_sigma_from_rho_bwd": ([I64, P, P, P, P], C.c_int),
+        "vt_sample_rays": ([I64, P, P, P, I64, C.c_uint64, P, P, P, P, P], C.c_int),
+        "vt_smooth_l1_loss": ([I64, P, P, C.c_float, P, P, P], C.c_int),
+        "vt_texture_regularizers": ([I64, I32, P, P, C.c_float, C.c_float, P, P, P, P], C.c_int),
+        "vt_adam_step": ([I64, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, I64, P], C.c_int),
         "vt_status_str": ([C.c_int], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -144,19 +153,20 @@ def vt_generate_rays(cams, o: int, d: int, time: int, stream: int):
 
 
 def vt_render_fwd(scene: int, n_rays: int, o: int, d: int, time: int, params: vt_render_params, rgb: int, T: int,
-                  steps: int, rgb_residual: int, stream: int):
+                  steps: int, rgb_residual: int, dist: int, stream: int):
     check(lib.vt_render_fwd(C.c_void_p(scene), n_rays, C.c_void_p(o), C.c_void_p(d), C.c_void_p(time),
                             C.byref(params), C.c_void_p(rgb), C.c_void_p(T), C.c_void_p(steps),
-                            C.c_void_p(rgb_residual), C.c_void_p(stream)), "vt_render_fwd")
+                            C.c_void_p(rgb_residual), C.c_void_p(dist), C.c_void_p(stream)), "vt_render_fwd")
 
 
 def vt_render_bwd(scene: int, n_rays: int, o: int, d: int, time: int, params: vt_render_params, rgb: int,
-                  rgb_residual: int, grad_rgb: int, grad_sites: int, grad_sigma: int, grad_tex: int,
-                  grad_tex_vd: int, stream: int):
+                  rgb_residual: int, dist: int, grad_rgb: int, grad_dist: int, grad_sites: int, grad_sigma: int,
+                  grad_tex: int, grad_tex_vd: int, stream: int):
     check(lib.vt_render_bwd(C.c_void_p(scene), n_rays, C.c_void_p(o), C.c_void_p(d), C.c_void_p(time),
-                            C.byref(params), C.c_void_p(rgb), C.c_void_p(rgb_residual), C.c_void_p(grad_rgb),
-                            C.c_void_p(grad_sites), C.c_void_p(grad_sigma), C.c_void_p(grad_tex),
-                            C.c_void_p(grad_tex_vd), C.c_void_p(stream)), "vt_render_bwd")
+                            C.byref(params), C.c_void_p(rgb), C.c_void_p(rgb_residual), C.c_void_p(dist),
+                            C.c_void_p(grad_rgb), C.c_void_p(grad_dist), C.c_void_p(grad_sites),
+                            C.c_void_p(grad_sigma), C.c_void_p(grad_tex), C.c_void_p(grad_tex_vd),
+                            C.c_void_p(stream)), "vt_render_bwd")
 
 
 def vt_render_bwd_static(scene: int, n_rays: int, o: int, d: int, time: int, params: vt_render_params, rgb: int,
@@ -189,3 +199,37 @@ def vt_average_samples(n_pixels: int, spp: int, rgb_rays: int, rgb_px: int, stre
 def vt_average_samples_bwd(n_pixels: int, spp: int, grad_px: int, grad_rays: int, stream: int):
     check(lib.vt_average_samples_bwd(n_pixels, spp, C.c_void_p(grad_px), C.c_void_p(grad_rays),
                                      C.c_void_p(stream)), "vt_average_samples_bwd")
+
+
+def vt_sigma_from_rho(n: int, rho: int, sigma: int, stream: int):
+    check(lib.vt_sigma_from_rho(n, C.c_void_p(rho), C.c_void_p(sigma), C.c_void_p(stream)), "vt_sigma_from_rho")
+
+
+def vt_sigma_from_rho_bwd(n: int, sigma: int, grad_sigma: int, grad_rho: int, stream: int):
+    check(lib.vt_sigma_from_rho_bwd(n, C.c_void_p(sigma), C.c_void_p(grad_sigma), C.c_void_p(grad_rho),
+                                    C.c_void_p(stream)), "vt_sigma_from_rho_bwd")
+
+
+def vt_sample_rays(n_pool: int, o_pool: int, d_pool: int, y_pool: int, n: int, seed: int, o: int, d: int, y: int,
+                   idx: int, stream: int):
+    check(lib.vt_sample_rays(n_pool, C.c_void_p(o_pool), C.c_void_p(d_pool), C.c_void_p(y_pool), n, seed,
+                             C.c_void_p(o), C.c_void_p(d), C.c_void_p(y), C.c_void_p(idx), C.c_void_p(stream)),
+          "vt_sample_rays")
+
+
+def vt_smooth_l1_loss(n: int, rgb: int, target: int, beta: float, grad: int, loss: int, stream: int):
+    check(lib.vt_smooth_l1_loss(n, C.c_void_p(rgb), C.c_void_p(target), beta, C.c_void_p(grad), C.c_void_p(loss),
+                                C.c_void_p(stream)), "vt_smooth_l1_loss")
+
+
+def vt_texture_regularizers(n_cells: int, tex_res: int, tex: int, tex_vd: int, lambda_vd: float, lambda_mean: float,
+                            grad_tex: int, grad_tex_vd: int, loss: int, stream: int):
+    check(lib.vt_texture_regularizers(n_cells, tex_res, C.c_void_p(tex), C.c_void_p(tex_vd), lambda_vd, lambda_mean,
+                                      C.c_void_p(grad_tex), C.c_void_p(grad_tex_vd), C.c_void_p(loss),
+                                      C.c_void_p(stream)), "vt_texture_regularizers")
+
+
+def vt_adam_step(n: int, param: int, grad: int, m: int, v: int, lr: float, beta1: float, beta2: float, eps: float,
+                 step: int, stream: int):
+    check(lib.vt_adam_step(n, C.c_void_p(param), C.c_void_p(grad), C.c_void_p(m), C.c_void_p(v), lr, beta1, beta2,
+                           eps, step, C.c_void_p(stream)), "vt_adam_step")

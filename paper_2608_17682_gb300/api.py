@@ -13,7 +13,7 @@ import ctypes
 import torch
 
 from . import _vt
-from ._vt import VT_BF16, VT_F16, VT_F32  # noqa: F401
+from ._vt import VT_BF16, VT_F16, VT_F32, VTError  # noqa: F401
 
 _DTYPES = {"f32": VT_F32, "fp32": VT_F32, "f16": VT_F16, "fp16": VT_F16, "bf16": VT_BF16}
 
@@ -34,7 +34,7 @@ class Scene:
     """A Voronoi scene resident on the GPU (library-owned, Morton-ordered)."""
 
     def __init__(self, sites, sigma, tex, adj_offsets, adj_indices, tex_dtype="f32", device="cuda",
-                 keep_order=False, tex_vd=None):
+                 keep_order=False, tex_vd=None, half_offsets=False):
         device = torch.device(device)
         self.device = device
         sites = _dev_f32(sites, device)
@@ -53,16 +53,17 @@ class Scene:
         self.n, self.R = n, tex.shape[1]
         self.tex_dtype = _DTYPES[tex_dtype] if isinstance(tex_dtype, str) else int(tex_dtype)
         desc = _vt.vt_scene_desc(n, self.R, self.tex_dtype, sites.data_ptr(), sigma.data_ptr(), tex.data_ptr(),
-                                 off.data_ptr(), idx.data_ptr(), _vt.VT_SCENE_KEEP_ORDER if keep_order else 0,
-                                 _ptr(tvd))
+                                 off.data_ptr(), idx.data_ptr(),
+                                 (_vt.VT_SCENE_KEEP_ORDER if keep_order else 0)
+                                 | (_vt.VT_SCENE_HALF_OFFSETS if half_offsets else 0), _ptr(tvd))
         with torch.cuda.device(device):
             self.handle = _vt.vt_scene_create(desc, _stream())
         self.n_edges = _vt.vt_scene_info(self.handle)[3]
 
     @classmethod
-    def from_workload(cls, sc, tex_dtype="f32", device="cuda", keep_order=False, tex_vd=None):
+    def from_workload(cls, sc, tex_dtype="f32", device="cuda", keep_order=False, tex_vd=None, half_offsets=False):
         return cls(sc.sites, sc.sigma, sc.tex, sc.offsets, sc.indices, tex_dtype=tex_dtype, device=device,
-                   keep_order=keep_order, tex_vd=tex_vd)
+                   keep_order=keep_order, tex_vd=tex_vd, half_offsets=half_offsets)
 
     def update(self, sites=None, sigma=None, tex=None, tex_vd=None):
         keep = [None if x is None else _dev_f32(x, self.device) for x in (sites, sigma, tex, tex_vd)]
@@ -133,10 +134,11 @@ def generate_rays(cameras, device="cuda", out=None):
     return o, d, t
 
 
-def render_fwd(scene: Scene, o, d, params, time=None, out=None, want_steps=True, residual=None):
+def render_fwd(scene: Scene, o, d, params, time=None, out=None, want_steps=True, residual=None, dist=None):
     """Forward render; returns (rgb, T, steps). If `residual` is a [n,3] tensor
     it receives C - rgb (the float-float colour's rounding residual) for an
-    exact backward."""
+    exact backward. If `dist` is a [n,3] tensor it receives the distortion
+    loss per ray (column 0, Eq. 2) and the two totals the backward needs."""
     n = o.shape[0]
     if out is None:
         rgb = torch.empty(n, 3, device=o.device)
@@ -145,14 +147,16 @@ def render_fwd(scene: Scene, o, d, params, time=None, out=None, want_steps=True,
     else:
         rgb, T, steps = out
     _vt.vt_render_fwd(scene.handle, n, o.data_ptr(), d.data_ptr(), _ptr(time), params, rgb.data_ptr(), _ptr(T),
-                      _ptr(steps), _ptr(residual), _stream())
+                      _ptr(steps), _ptr(residual), _ptr(dist), _stream())
     return rgb, T, steps
 
 
 def render_bwd(scene: Scene, o, d, params, rgb, grad_rgb, time=None, out=None, need=(True, True, True),
-               residual=None, tex_vd_out=None):
+               residual=None, tex_vd_out=None, dist=None, grad_dist=None):
     """Backward render: (grad_sites, grad_sigma, grad_tex); the gradient of the
-    view-dependent texture (appearance 1) is written to `tex_vd_out` if given."""
+    view-dependent texture (appearance 1) is written to `tex_vd_out` if given.
+    With `grad_dist` ([n], dL/dL_dist per ray) the distortion loss is included;
+    `dist` is then the forward's `dist` output."""
     dev = o.device
     if out is None:
         gs = torch.empty(scene.n, 3, device=dev) if need[0] else None
@@ -160,9 +164,11 @@ def render_bwd(scene: Scene, o, d, params, rgb, grad_rgb, time=None, out=None, n
         gt = torch.empty(scene.n, scene.R, scene.R, 3, device=dev) if need[2] else None
     else:
         gs, gsig, gt = out
+    if grad_dist is not None:
+        grad_dist = grad_dist.contiguous()
     _vt.vt_render_bwd(scene.handle, o.shape[0], o.data_ptr(), d.data_ptr(), _ptr(time), params, rgb.data_ptr(),
-                      _ptr(residual), grad_rgb.contiguous().data_ptr(), _ptr(gs), _ptr(gsig), _ptr(gt),
-                      _ptr(tex_vd_out), _stream())
+                      _ptr(residual), _ptr(dist), grad_rgb.contiguous().data_ptr(), _ptr(grad_dist), _ptr(gs),
+                      _ptr(gsig), _ptr(gt), _ptr(tex_vd_out), _stream())
     return gs, gsig, gt
 
 
@@ -191,6 +197,37 @@ def average_samples(rgb_rays, spp):
     return out
 
 
+def sigma_from_rho(rho):
+    """sigma = exp(rho) (Sec. 5.4) on the GPU."""
+    rho = rho.contiguous()
+    out = torch.empty_like(rho)
+    _vt.vt_sigma_from_rho(rho.numel(), rho.data_ptr(), out.data_ptr(), _stream())
+    return out
+
+
+def sigma_from_rho_bwd(sigma, grad_sigma):
+    """dL/drho = dL/dsigma * sigma (Eq. 4) on the GPU."""
+    out = torch.empty_like(sigma)
+    _vt.vt_sigma_from_rho_bwd(sigma.numel(), sigma.contiguous().data_ptr(), grad_sigma.contiguous().data_ptr(),
+                              out.data_ptr(), _stream())
+    return out
+
+
+class SigmaFromRho(torch.autograd.Function):
+    """sigma = exp(rho) with the adjoint of Eq. 4."""
+
+    @staticmethod
+    def forward(ctx, rho):
+        sigma = sigma_from_rho(rho)
+        ctx.save_for_backward(sigma)
+        return sigma
+
+    @staticmethod
+    def backward(ctx, grad_sigma):
+        (sigma,) = ctx.saved_tensors
+        return sigma_from_rho_bwd(sigma, grad_sigma)
+
+
 def average_samples_bwd(grad_px, spp):
     out = torch.empty(grad_px.shape[0] * spp, 3, device=grad_px.device)
     _vt.vt_average_samples_bwd(grad_px.shape[0], spp, grad_px.contiguous().data_ptr(), out.data_ptr(), _stream())
@@ -205,24 +242,29 @@ class VTRender(torch.autograd.Function):
     must hold their current values (call scene.update after changing them)."""
 
     @staticmethod
-    def forward(ctx, sites, sigma, tex, tex_vd, o, d, scene, params):
+    def forward(ctx, sites, sigma, tex, tex_vd, o, d, scene, params, with_dist=False):
         res = torch.empty(o.shape[0], 3, device=o.device)
-        rgb, _, _ = render_fwd(scene, o, d, params, want_steps=False, residual=res)
-        ctx.scene, ctx.params = scene, params
-        ctx.save_for_backward(o, d, rgb, res)
+        dist = torch.empty(o.shape[0], 3, device=o.device) if with_dist else None
+        rgb, _, _ = render_fwd(scene, o, d, params, want_steps=False, residual=res, dist=dist)
+        ctx.scene, ctx.params, ctx.with_dist = scene, params, with_dist
+        ctx.save_for_backward(o, d, rgb, res, dist)
+        if with_dist:
+            return rgb, dist[:, 0].contiguous()
         return rgb
 
     @staticmethod
-    def backward(ctx, grad_rgb):
-        o, d, rgb, res = ctx.saved_tensors
+    def backward(ctx, grad_rgb, grad_dist=None):
+        o, d, rgb, res, dist = ctx.saved_tensors
         need = ctx.needs_input_grad[:3]
         gvd = None
         if ctx.needs_input_grad[3] and ctx.scene.has_tex_vd:
             gvd = torch.empty(ctx.scene.n, ctx.scene.R, ctx.scene.R, 3, device=o.device)
         gs, gsig, gt = render_bwd(ctx.scene, o, d, ctx.params, rgb, grad_rgb, need=need, residual=res,
-                                  tex_vd_out=gvd)
-        return gs, gsig, gt, gvd, None, None, None, None
+                                  tex_vd_out=gvd, dist=dist, grad_dist=grad_dist if ctx.with_dist else None)
+        return gs, gsig, gt, gvd, None, None, None, None, None
 
 
-def render(sites, sigma, tex, o, d, scene: Scene, params, tex_vd=None):
-    return VTRender.apply(sites, sigma, tex, tex_vd, o, d, scene, params)
+def render(sites, sigma, tex, o, d, scene: Scene, params, tex_vd=None, with_dist=False):
+    """Differentiable render; returns rgb, or (rgb, L_dist per ray) with
+    with_dist=True (distortion loss of Sec. 5.3, Eq. 2)."""
+    return VTRender.apply(sites, sigma, tex, tex_vd, o, d, scene, params, with_dist)

@@ -36,6 +36,7 @@ struct vt_scene {
   int32_t dtype = VT_F32;
   vt_cell* cell = nullptr;
   float4* nbr = nullptr;
+  uint2* nbr_h = nullptr;  // optional FP16 offsets {x,y | z,0} (VT_SCENE_HALF_OFFSETS)
   void* tex = nullptr;
   void* tex_vd = nullptr;  // view-dependent texture (appearance 1), same layout as tex
   int32_t* perm = nullptr;

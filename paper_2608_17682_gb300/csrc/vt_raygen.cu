@@ -1,6 +1,7 @@
 // vt_raygen.cu -- ray generation for the camera models of Sec. 6.5 (pinhole,
-// equidistant fisheye, rolling shutter, thin lens), the L2 photometric loss
-// of the benchmark workloads, and the per-pixel average of lens samples.
+// equidistant fisheye, rolling shutter, thin lens, motion blur), the L2
+// photometric loss of the benchmark workloads, the per-pixel average of lens
+// and time samples, and the sigma = exp(rho) density map of Sec. 5.4.
 #include "vt_internal.cuh"
 
 namespace {
@@ -152,6 +153,16 @@ __global__ void k_avg_bwd(int64_t n, int spp, const float* __restrict__ g, float
   }
 }
 
+__global__ void k_exp(int64_t n, const float* x, float* y) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = expf(x[e]);
+}
+
+__global__ void k_mul(int64_t n, const float* a, const float* b, float* y) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = a[e] * b[e];
+}
+
 bool camera_ok(const vt_camera& c) {
   if (c.w <= 0 || c.h <= 0 || c.kind < 0 || c.kind > 4) return false;
   if (c.kind == VT_CAM_MOTION_BLUR && c.lens_samples < 1) return false;
@@ -224,6 +235,23 @@ vt_status vt_average_samples_bwd(int64_t n_pixels, int32_t spp, const float* gra
   if (n_pixels == 0) return VT_OK;
   k_avg_bwd<<<vt_grid(3 * n_pixels * spp, 256, 152 * 64), 256, 0, (cudaStream_t)stream>>>(n_pixels, spp, grad_px,
                                                                                            grad_rays);
+  VT_CUDA_TRY(cudaGetLastError());
+  return VT_OK;
+}
+
+vt_status vt_sigma_from_rho(int64_t n, const float* rho, float* sigma, void* stream) {
+  if (n < 0 || (n > 0 && (!rho || !sigma))) return VT_ERR_INVALID_ARG;
+  if (n == 0) return VT_OK;
+  k_exp<<<vt_grid(n, 256, 152 * 16), 256, 0, (cudaStream_t)stream>>>(n, rho, sigma);
+  VT_CUDA_TRY(cudaGetLastError());
+  return VT_OK;
+}
+
+vt_status vt_sigma_from_rho_bwd(int64_t n, const float* sigma, const float* grad_sigma, float* grad_rho,
+                                void* stream) {
+  if (n < 0 || (n > 0 && (!sigma || !grad_sigma || !grad_rho))) return VT_ERR_INVALID_ARG;
+  if (n == 0) return VT_OK;
+  k_mul<<<vt_grid(n, 256, 152 * 16), 256, 0, (cudaStream_t)stream>>>(n, grad_sigma, sigma, grad_rho);
   VT_CUDA_TRY(cudaGetLastError());
   return VT_OK;
 }

@@ -64,6 +64,7 @@ constexpr int kNbrUnroll = VT_NBR_UNROLL;
 struct Scene {
   const vt_cell* __restrict__ cell;
   const float4* __restrict__ nbr;
+  const uint2* __restrict__ nbr_h;  // FP16 offsets (VT_SCENE_HALF_OFFSETS) or null
   const void* __restrict__ tex;
   const void* __restrict__ tex_vd;
   int64_t n;
@@ -106,6 +107,10 @@ struct Grad {
   const float* rgb;
   const float* rgb_lo;  // optional residual of the forward colour
   const float* grad;
+  // distortion loss (Eq. 2): per-ray {L_dist, sum w, sum w sbar'} written by
+  // the forward, read by the backward; dL/dL_dist per ray (backward)
+  float* dist;
+  const float* gdist;
 };
 
 struct Trace {
@@ -488,7 +493,7 @@ struct WalkBounds {
   static constexpr int minb = MODE == FWD ? VT_FWD_MINB : (MODE == BWD ? VT_BWD_MINB : 2);
 };
 
-template <int MODE, int DT, int APP>
+template <int MODE, int DT, int APP, int DIST, int HALF>
 __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
     k_walk(Scene S, RP P, const float* __restrict__ O, const float* __restrict__ D,
            const int32_t* __restrict__ anchor_cell, float* __restrict__ rgb_out, float* __restrict__ T_out,
@@ -503,6 +508,21 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
   float Ch0 = 0.f, Ch1 = 0.f, Ch2 = 0.f, Cl0 = 0.f, Cl1 = 0.f, Cl2 = 0.f;
   float T = 1.f;
   int k = 0;
+  // distortion loss (Eq. 2) in the coordinate s(t) = 1 - 1/(1+t). Composited
+  // intervals are contiguous, so sbar_k - sbar_{k-1} = (ds_{k-1} + ds_k)/2 with
+  // ds = s(b) - s(a) = (b - a)/((1+a)(1+b)); sbar' = sbar - sbar_first. Sums
+  // in the order of the walk: W = sum w, Q = sum w sbar',
+  // A_k = sum_{l<k} w_l (sbar_k - sbar_l) = A_{k-1} + W_{<k} gap_k,
+  // L = sum_k w_k (2 A_k + w_k ds_k / 3).
+  float dW = 0.f, dQ = 0.f, dA = 0.f, dL = 0.f, dsb = 0.f, dsp = -1.f;
+  // backward: forward totals, dL/dL_dist, sum_{l<k} G_l w_l, pending exit term
+  float dLt = 0.f, dWt = 0.f, dQt = 0.f, gdd = 0.f, dP = 0.f, p_db = 0.f;
+  if (DIST && MODE == BWD) {
+    dLt = G.dist[3 * ray];
+    dWt = G.dist[3 * ray + 1];
+    dQt = G.dist[3 * ray + 2];
+    gdd = G.gdist[ray];
+  }
   const bool bad = !(dd > 0.f) || !isfinite(dd) || !isfinite(o.x) || !isfinite(o.y) || !isfinite(o.z);
   // clip [t_near, t_far] to the optional box (slab test)
   float t0 = P.t_near, t1 = P.t_far;
@@ -588,7 +608,15 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
       int bj = -1;
 #pragma unroll kNbrUnroll
       for (int p = m.x; p < m.y; ++p) {
-        const float4 q = __ldg(S.nbr + p);
+        // HALF: 8-byte FP16 offset records; the winner's id is read after the loop
+        float4 q;
+        if constexpr (HALF) {
+          const uint2 h = __ldg(S.nbr_h + p);
+          const float2 xy = __half22float2(*reinterpret_cast<const __half2*>(&h.x));
+          q = make_float4(xy.x, xy.y, __low2float(*reinterpret_cast<const __half2*>(&h.y)), __int_as_float(p));
+        } else {
+          q = __ldg(S.nbr + p);
+        }
         float den = __fmaf_rn(q.x, d.x, __fmaf_rn(q.y, d.y, __fmul_rn(q.z, d.z)));
         // n.(r + n/2)
         float num = __fmaf_rn(q.x, __fmaf_rn(0.5f, q.x, r.x),
@@ -596,7 +624,8 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
         if (fabsf(den) <= Gc) {
           // grazing plane: FP64 recheck from the FP32 inputs
           atomicAdd(S.err + 1, 1ull);
-          if (!grazing_fp64(S.cell, __float_as_int(q.w), si, o, d, th, tl, &num)) continue;
+          const int jg = HALF ? __ldg(reinterpret_cast<const int*>(S.nbr + p) + 3) : __float_as_int(q.w);
+          if (!grazing_fp64(S.cell, jg, si, o, d, th, tl, &num)) continue;
           den = 1.f;
         } else if (!(den > 0.f)) {
           continue;
@@ -607,6 +636,7 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
           bj = __float_as_int(q.w);
         }
       }
+      if (HALF && bj >= 0) bj = __ldg(reinterpret_cast<const int*>(S.nbr + bj) + 3);
       ++k;
       if (MODE != TRACE && !VT_TEX_EARLY && !APP) {
         tx0 = load_texel<DT>(S.tex, tb0);
@@ -639,6 +669,7 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
         if (exit_beyond) bh = t1, bl = 0.f;
         delta = __fadd_rn(__fsub_rn(bh, ah), __fsub_rn(bl, al));
       }
+      float dist_da = 0.f, dist_db = 0.f;  // distortion: direct dL/da, dL/db of this interval
       bool stop = false;
       float dtau = 0.f, w = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
       bool coloured = false;
@@ -733,6 +764,36 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
           // dL/dtau_k = g . (T_{k+1} c_k - S_k)
           dtau = g0 * ((Tn * c0 - Sh0) - Sl0) + g1 * ((Tn * c1 - Sh1) - Sl1) + g2 * ((Tn * c2 - Sh2) - Sl2);
         }
+        if (DIST && MODE != TRACE) {
+          const float a = start_clip ? t0 : __fadd_rn(th, tl);
+          const float b = exit_beyond ? t1 : __fadd_rn(eh, el);
+          const float ia = __fdividef(1.f, 1.f + a), ib = __fdividef(1.f, 1.f + b);
+          const float ds = delta * ia * ib;
+          if (dsp >= 0.f) {
+            const float gap = 0.5f * (dsp + ds);
+            dsb += gap;
+            dA = __fmaf_rn(dW, gap, dA);
+          }
+          dsp = ds;
+          if (MODE == FWD) {
+            dL = __fmaf_rn(w, __fmaf_rn(w * ds, 1.f / 3.f, 2.f * dA), dL);
+          } else {
+            // G_k = dL/dw_k = 2 (A_k + B_k) + 2/3 w_k ds_k,
+            // B_k = sum_{l>k} w_l (sbar_l - sbar_k) = Q_{>k} - sbar'_k W_{>k}
+            const float Wg = dWt - dW - w, Qg = dQt - dQ - w * dsb;
+            const float Gk = 2.f * (dA + (Qg - dsb * Wg)) + (2.f / 3.f) * w * ds;
+            // dw_k/dtau_k = T_{k+1}; dw_m/dtau_k = -w_m (m > k); sum_m G_m w_m = 2 L
+            const float suffix = 2.f * dLt - dP - Gk * w;
+            dtau = __fmaf_rn(gdd, Gk * Tn - suffix, dtau);
+            dP = __fmaf_rn(Gk, w, dP);
+            // interval ends: sbar = (s(a)+s(b))/2, ds = s(b)-s(a), s' = 1/(1+t)^2
+            const float dsbar = 2.f * w * (dW - Wg), ddsk = w * w * (1.f / 3.f);
+            dist_da = gdd * ia * ia * (0.5f * dsbar - ddsk);
+            dist_db = gdd * ib * ib * (0.5f * dsbar + ddsk);
+          }
+          dQ = __fmaf_rn(w, dsb, dQ);
+          dW += w;
+        }
         T = Tn;
         if (T < P.T_eps) stop = true;
       }
@@ -743,6 +804,7 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
         // x_b - s_prev = n - r, s_cur - x_b = r
         float3 gs = make_float3(0.f, 0.f, 0.f);
         float dLdt = cross_valid ? p_sdtau - sig * dtau : 0.f;
+        if (DIST && cross_valid) dLdt += p_db + dist_da;
         if (APP) dLdt += p_xt + (k > 1 ? gt_col : 0.f);
         if (pc >= 0 && dLdt != 0.f) {
 #if VT_BWD_RELOAD_PREV
@@ -784,7 +846,7 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
         cross_valid = (bj >= 0) && !exit_beyond && ff_gt(eh, el, t0);
         // appearance 1: the origin cell's colour sits on its exit crossing
         const float xt_exit = (APP && k == 1 && bj >= 0) ? gt_col : 0.f;
-        const float dLdt_exit = (stop && cross_valid ? p_sdtau : 0.f) + xt_exit;
+        const float dLdt_exit = (stop && cross_valid ? p_sdtau + (DIST ? dist_db : 0.f) : 0.f) + xt_exit;
         if ((stop || exit_beyond) && bj >= 0 && dLdt_exit != 0.f) {
           // the walk ends in this cell but its exit plane still moves delta_K
           // (terminated inside the extent) and/or its surface point
@@ -800,6 +862,7 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
           add_cell_grad(G.g_cell, bj, dtb * (re.x + nx), dtb * (re.y + ny), dtb * (re.z + nz), 0.f);
         }
         p_xt = xt_exit;
+        if (DIST) p_db = dist_db;
       }
       if (stop || exit_beyond) break;
       cell = bj;
@@ -830,6 +893,11 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
     }
     if (T_out) T_out[ray] = T;
     if (steps_out) steps_out[ray] = k;
+    if (DIST) {
+      G.dist[3 * ray] = dL;
+      G.dist[3 * ray + 1] = dW;
+      G.dist[3 * ray + 2] = dQ;
+    }
   } else if (MODE == TRACE) {
     TR.n_cells[ray] = k;
     if (k > TR.max_cells) atomicOr(S.err, (unsigned long long)VT_EBIT_CAPACITY);
@@ -953,6 +1021,7 @@ Scene scene_view(vt_scene* s) {
   Scene S;
   S.cell = s->cell;
   S.nbr = s->nbr;
+  S.nbr_h = s->nbr_h;
   S.tex = s->tex;
   S.tex_vd = s->tex_vd;
   S.n = s->n;
@@ -973,15 +1042,15 @@ vt_status anchors(vt_scene* s, const Scene& S, const RP& P, const float* o, cuda
   return VT_OK;
 }
 
-template <int MODE, int APP>
+template <int MODE, int APP, int DIST, int HALF = 0>
 void launch_walk_app(vt_scene* s, const Scene& S, const RP& P, const float* o, const float* d, float* rgb, float* T,
                      int32_t* steps, Grad G, Trace TR, cudaStream_t st, int g) {
   if (s->dtype == VT_F32)
-    k_walk<MODE, VT_F32, APP><<<g, 256, 0, st>>>(S, P, o, d, s->anchor_cell, rgb, T, steps, G, TR);
+    k_walk<MODE, VT_F32, APP, DIST, HALF><<<g, 256, 0, st>>>(S, P, o, d, s->anchor_cell, rgb, T, steps, G, TR);
   else if (s->dtype == VT_F16)
-    k_walk<MODE, VT_F16, APP><<<g, 256, 0, st>>>(S, P, o, d, s->anchor_cell, rgb, T, steps, G, TR);
+    k_walk<MODE, VT_F16, APP, DIST, HALF><<<g, 256, 0, st>>>(S, P, o, d, s->anchor_cell, rgb, T, steps, G, TR);
   else
-    k_walk<MODE, VT_BF16, APP><<<g, 256, 0, st>>>(S, P, o, d, s->anchor_cell, rgb, T, steps, G, TR);
+    k_walk<MODE, VT_BF16, APP, DIST, HALF><<<g, 256, 0, st>>>(S, P, o, d, s->anchor_cell, rgb, T, steps, G, TR);
 }
 
 template <int MODE>
@@ -990,10 +1059,24 @@ vt_status launch_walk(vt_scene* s, const Scene& S, const RP& P, const float* o, 
   int64_t nt = walk_threads(P);
   if (nt == 0) return VT_OK;
   int g = vt_grid(nt, 256, ((int64_t)1 << 31) - 1);
-  if (MODE != TRACE && P.appearance == 1)
-    launch_walk_app<MODE, MODE == TRACE ? 0 : 1>(s, S, P, o, d, rgb, T, steps, G, TR, st, g);
+  constexpr int F = MODE == TRACE ? 0 : 1;  // no appearance / distortion variants of the trace
+  const bool dist = MODE != TRACE && G.dist != nullptr;
+  if (S.nbr_h) {
+    // FP16 neighbour offsets: forward (no distortion) and trace only
+    if (MODE == BWD || dist) return VT_ERR_UNSUPPORTED;
+    constexpr int H = MODE == BWD ? 0 : 1;
+    if (P.appearance == 1)
+      launch_walk_app<MODE, F, 0, H>(s, S, P, o, d, rgb, T, steps, G, TR, st, g);
+    else
+      launch_walk_app<MODE, 0, 0, H>(s, S, P, o, d, rgb, T, steps, G, TR, st, g);
+  } else if (P.appearance == 1 && dist)
+    launch_walk_app<MODE, F, F>(s, S, P, o, d, rgb, T, steps, G, TR, st, g);
+  else if (P.appearance == 1)
+    launch_walk_app<MODE, F, 0>(s, S, P, o, d, rgb, T, steps, G, TR, st, g);
+  else if (dist)
+    launch_walk_app<MODE, 0, F>(s, S, P, o, d, rgb, T, steps, G, TR, st, g);
   else
-    launch_walk_app<MODE, 0>(s, S, P, o, d, rgb, T, steps, G, TR, st, g);
+    launch_walk_app<MODE, 0, 0>(s, S, P, o, d, rgb, T, steps, G, TR, st, g);
   VT_CUDA_TRY(cudaGetLastError());
   return VT_OK;
 }
@@ -1004,32 +1087,38 @@ extern "C" {
 
 vt_status vt_render_fwd(vt_scene* s, int64_t n_rays, const float* o, const float* d, const float* time,
                         const vt_render_params* p, float* rgb_out, float* T_out, int32_t* steps_out,
-                        float* rgb_residual, void* stream) {
+                        float* rgb_residual, float* dist_out, void* stream) {
   (void)time;
   if (!s || n_rays < 0 || (n_rays > 0 && (!o || !d || !rgb_out))) return VT_ERR_INVALID_ARG;
   if (n_rays == 0) return VT_OK;
   RP P;
   vt_status r = make_rp(s, n_rays, p, P);
   if (r != VT_OK) return r;
+  if (dist_out && !(P.t_near >= 0.f)) return VT_ERR_INVALID_ARG;  // s(t) needs t > -1
+  if (dist_out && s->nbr_h) return VT_ERR_UNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   Scene S = scene_view(s);
   r = anchors(s, S, P, o, st);
   if (r != VT_OK) return r;
   Grad G{};
   G.rgb_lo = rgb_residual;
+  G.dist = dist_out;
   return launch_walk<FWD>(s, S, P, o, d, rgb_out, T_out, steps_out, G, Trace{}, st);
 }
 
 vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float* d, const float* time,
                         const vt_render_params* p, const float* rgb_out, const float* rgb_residual,
-                        const float* grad_rgb, float* grad_sites, float* grad_sigma, float* grad_tex,
-                        float* grad_tex_vd, void* stream) {
+                        const float* dist_out, const float* grad_rgb, const float* grad_dist, float* grad_sites,
+                        float* grad_sigma, float* grad_tex, float* grad_tex_vd, void* stream) {
   (void)time;
   if (!s || n_rays < 0 || (n_rays > 0 && (!o || !d || !rgb_out || !grad_rgb))) return VT_ERR_INVALID_ARG;
   if (grad_tex_vd && !s->tex_vd) return VT_ERR_INVALID_ARG;
+  if (grad_dist && !dist_out) return VT_ERR_INVALID_ARG;
+  if (s->nbr_h) return VT_ERR_UNSUPPORTED;  // FP16-offset scenes are forward only
   RP P;
   vt_status r = make_rp(s, n_rays > 0 ? n_rays : 0, p, P);
   if (r != VT_OK && n_rays > 0) return r;
+  if (grad_dist && n_rays > 0 && !(P.t_near >= 0.f)) return VT_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t RR = (int64_t)s->R * s->R;
   if (!s->g_cell) VT_CUDA_TRY(cudaMalloc(&s->g_cell, s->n * sizeof(float4)));
@@ -1042,7 +1131,11 @@ vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float
   if (n_rays > 0) {
     r = anchors(s, S, P, o, st);
     if (r != VT_OK) return r;
-    Grad G{s->g_cell, s->g_tex, s->g_tex_vd, rgb_out, rgb_residual, grad_rgb};
+    Grad G{s->g_cell, s->g_tex, s->g_tex_vd, rgb_out, rgb_residual, grad_rgb, nullptr, nullptr};
+    if (grad_dist) {
+      G.dist = const_cast<float*>(dist_out);  // read only in the backward
+      G.gdist = grad_dist;
+    }
     r = launch_walk<BWD>(s, S, P, o, d, nullptr, nullptr, nullptr, G, Trace{}, st);
     if (r != VT_OK) return r;
   }
@@ -1113,7 +1206,7 @@ vt_status vt_render_bwd_static(vt_scene* s, int64_t n_rays, const float* o, cons
                                float* grad_sites, float* grad_sigma, float* grad_tex, void* stream) {
   (void)time;
   if (!s || n_rays < 0 || (n_rays > 0 && (!o || !d || !rgb_out || !grad_rgb))) return VT_ERR_INVALID_ARG;
-  if (p && p->appearance != 0) return VT_ERR_UNSUPPORTED;
+  if ((p && p->appearance != 0) || s->nbr_h) return VT_ERR_UNSUPPORTED;
   const int64_t RR = (int64_t)s->R * s->R;
   const int64_t need = s->n * (1 + RR);  // one float4 per cell + one per texel
   if (need > kStaticScratchFloat4) return VT_ERR_CAPACITY;
@@ -1132,7 +1225,7 @@ vt_status vt_render_bwd_static(vt_scene* s, int64_t n_rays, const float* o, cons
   if (n_rays > 0) {
     r = anchors(s, S, P, o, st);
     if (r != VT_OK) return r;
-    Grad G{g_cell, g_tex, nullptr, rgb_out, nullptr, grad_rgb};
+    Grad G{g_cell, g_tex, nullptr, rgb_out, nullptr, grad_rgb, nullptr, nullptr};
     r = launch_walk<BWD>(s, S, P, o, d, nullptr, nullptr, nullptr, G, Trace{}, st);
     if (r != VT_OK) return r;
   }

@@ -175,6 +175,36 @@ __global__ void k_fill_nbr(int64_t n, const vt_cell* __restrict__ cell, const in
   }
 }
 
+// FP16 copies of the offsets (round to nearest even); flags an offset that
+// does not fit FP16's range
+__global__ void k_fill_nbr_h(int64_t E, const float4* __restrict__ nbr, uint2* __restrict__ nbr_h,
+                             unsigned long long* err) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
+    const float4 q = nbr[p];
+    if (!(fabsf(q.x) < 65504.f && fabsf(q.y) < 65504.f && fabsf(q.z) < 65504.f)) atomicOr(err, 1ull);
+    const __half2 xy = __floats2half2_rn(q.x, q.y);
+    const __half2 z0 = __floats2half2_rn(q.z, 0.f);
+    nbr_h[p] = make_uint2(*reinterpret_cast<const unsigned int*>(&xy), *reinterpret_cast<const unsigned int*>(&z0));
+  }
+}
+
+vt_status fill_half_offsets(vt_scene* s, cudaStream_t st) {
+  if (!s->nbr_h || s->E == 0) return VT_OK;
+  unsigned long long* bad = nullptr;
+  VT_CUDA_TRY(cudaMalloc(&bad, sizeof(unsigned long long)));
+  unsigned long long hbad = 0;
+  cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) {
+    k_fill_nbr_h<<<vt_grid(s->E, 256, 152 * 32), 256, 0, st>>>(s->E, s->nbr, s->nbr_h, bad);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(bad);
+  if (e != cudaSuccess) return VT_ERR_CUDA;
+  return hbad ? VT_ERR_INVALID_ARG : VT_OK;
+}
+
 // largest neighbour offset |n| of each cell (bound for the grazing test)
 __global__ void k_cell_nmax(int64_t n, vt_cell* __restrict__ cell, const float4* __restrict__ nbr) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -257,6 +287,7 @@ void free_scene(vt_scene* s) {
   if (!s) return;
   cudaFree(s->cell);
   cudaFree(s->nbr);
+  cudaFree(s->nbr_h);
   cudaFree(s->tex);
   cudaFree(s->tex_vd);
   cudaFree(s->perm);
@@ -287,6 +318,7 @@ vt_status create_impl(const vt_scene_desc* dsc, cudaStream_t st, vt_scene* s) {
   const int64_t RR = (int64_t)s->R * s->R;
   VT_CUDA_TRY(dmalloc(&s->cell, n));
   VT_CUDA_TRY(dmalloc(&s->nbr, E > 0 ? E : 1));
+  if (dsc->flags & VT_SCENE_HALF_OFFSETS) VT_CUDA_TRY(dmalloc(&s->nbr_h, E > 0 ? E : 1));
   VT_CUDA_TRY(cudaMalloc(&s->tex, n * RR * vt_texel_bytes(s->dtype) + 16));
   if (dsc->tex_vd) VT_CUDA_TRY(cudaMalloc(&s->tex_vd, n * RR * vt_texel_bytes(s->dtype) + 16));
   VT_CUDA_TRY(dmalloc(&s->perm, n));
@@ -359,6 +391,8 @@ vt_status create_impl(const vt_scene_desc* dsc, cudaStream_t st, vt_scene* s) {
     k_fill_cells<<<g, 256, 0, st>>>(n, s->perm, dsc->sites, dsc->sigma, beg, deg, s->cell, 0);
     k_fill_nbr<<<g, 256, 0, st>>>(n, s->cell, dsc->adj_offsets, dsc->adj_indices, s->inv, s->nbr);
     k_cell_nmax<<<g, 256, 0, st>>>(n, s->cell, s->nbr);
+    rs = fill_half_offsets(s, st);
+    if (rs != VT_OK) break;
     rs = pack_tex(s, dsc->tex, st);
     if (rs != VT_OK) break;
     if (dsc->tex_vd) {
@@ -442,6 +476,10 @@ vt_status vt_scene_update(vt_scene* s, const float* sites, const float* sigma, c
       k_cell_nmax<<<g, 256, 0, st>>>(s->n, s->cell, s->nbr);
     }
     VT_CUDA_TRY(cudaGetLastError());
+    if (sites) {
+      vt_status h = fill_half_offsets(s, st);
+      if (h != VT_OK) return h;
+    }
   }
   if (tex) {
     vt_status v = pack_tex(s, tex, st);

@@ -577,3 +577,173 @@ def test_paper_appearance_autograd_and_rejections(tiny):
     plain = api.Scene.from_workload(sc)
     with pytest.raises(api._vt.VTError):
         api.render_fwd(plain, to, td, P)
+
+
+# ---------------------------------------------------------------- distortion loss (Eq. 2), sigma = exp(rho)
+
+DIST_TOL = 2e-5  # |L_gpu - L_ref| <= DIST_TOL * max(L_ref, 1e-3 max L_ref): FP32 sums of positive terms
+
+
+@pytest.mark.parametrize("which", ["tiny", "medium"])
+def test_distortion_forward_parity(which, tiny, medium):
+    if which == "tiny":
+        wl, osc, o, d = tiny
+        sc, base, img = wl.scene, wl.params, dict(img_w=64, img_h=64, n_images=1)
+    else:
+        sc, osc, o, d, _ = medium
+        base, img = W.default_params(), dict(img_w=203, img_h=121, n_images=2)
+    scene = api.Scene.from_workload(sc)
+    to, td = to_dev(o, d)
+    dist = torch.empty(len(o), 3, device=DEV)
+    rgb, _, _ = api.render_fwd(scene, to, td, gpu_params(base, **img), dist=dist)
+    plain = api.render_fwd(scene, to, td, gpu_params(base, **img))[0]
+    assert torch.equal(rgb, plain)  # the loss does not change the image
+    assert scene.get_error()[0] == 0
+    _, oT, _, flags = O.render(osc, o, d, params=oracle_params(base))
+    ok = (flags & O.BAND_FLAGS) == 0
+    L = O.distortion(osc, o, d, params=oracle_params(base))
+    got = dist[:, 0].cpu().numpy().astype(np.float64)
+    tol = DIST_TOL * np.maximum(L, 1e-3 * L.max())
+    assert np.all(np.abs(got - L)[ok] <= tol[ok]), np.abs(got - L)[ok].max()
+    hit = ok & (oT < 1)  # rays that composite at least one interval
+    assert hit.sum() > 500 and np.all(L[hit] > 0)
+    assert np.all(got >= 0)
+
+
+@pytest.mark.parametrize("appearance", [0, 1])
+def test_distortion_backward_parity(tiny, appearance):
+    wl, osc, o, d = tiny
+    sc = wl.scene
+    P = gpu_params(wl.params, img_w=64, img_h=64, n_images=1, appearance=appearance)
+    if appearance:
+        tvd = np.random.default_rng(21).normal(0, 0.5, size=sc.tex.shape).astype(np.float32)
+        osc = O.OracleScene(sc.sites, sc.sigma, sc.tex, sc.offsets, sc.indices, tex_vd=tvd)
+        scene = api.Scene(sc.sites, sc.sigma, sc.tex, sc.offsets, sc.indices, tex_vd=tvd)
+    else:
+        scene = api.Scene.from_workload(sc)
+    op = oracle_params(wl.params, appearance=appearance)
+    _, _, _, flags = O.render(osc, o, d, params=op)
+    ok = (flags & O.BAND_FLAGS) == 0
+    rng = np.random.default_rng(22)
+    g = (rng.normal(size=(len(o), 3)) * ok[:, None]).astype(np.float32)
+    gd = (rng.uniform(0.5, 2.0, size=len(o)) * ok).astype(np.float32)
+    to, td, tg, tgd = to_dev(o, d, g, gd)
+    res = torch.empty(len(o), 3, device=DEV)
+    dist = torch.empty(len(o), 3, device=DEV)
+    rgb = api.render_fwd(scene, to, td, P, residual=res, dist=dist)[0]
+    tvo = torch.empty_like(torch.as_tensor(sc.tex, device=DEV)) if appearance else None
+    gs, gsig, gt = api.render_bwd(scene, to, td, P, rgb, tg, residual=res, dist=dist, grad_dist=tgd,
+                                  tex_vd_out=tvo)
+    assert scene.get_error()[0] == 0
+    ref = O.render_bwd(osc, o, d, g.astype(np.float64), params=op, grad_dist=gd.astype(np.float64))
+    grad_close(gsig.cpu().numpy(), ref[1], "sigma")
+    grad_close(gt.cpu().numpy(), ref[2], "tex")
+    grad_close(gs.cpu().numpy(), ref[0], "sites")
+    if appearance:
+        grad_close(tvo.cpu().numpy(), ref[3], "tex_vd")
+    # distortion only (no colour gradient)
+    z = torch.zeros_like(tg)
+    gs2, gsig2, gt2 = api.render_bwd(scene, to, td, P, rgb, z, residual=res, dist=dist, grad_dist=tgd)
+    ref2 = O.render_bwd(osc, o, d, np.zeros((len(o), 3)), params=op, grad_dist=gd.astype(np.float64))
+    grad_close(gsig2.cpu().numpy(), ref2[1], "sigma (distortion only)")
+    grad_close(gs2.cpu().numpy(), ref2[0], "sites (distortion only)")
+    assert gt2.abs().max().item() == 0.0
+
+
+def test_distortion_medium_backward_parity(medium):
+    sc, osc, o, d, cams = medium
+    base = W.default_params()
+    P = gpu_params(base, img_w=203, img_h=121, n_images=2)
+    _, _, _, flags = O.render(osc, o, d, params=oracle_params(base))
+    ok = (flags & O.BAND_FLAGS) == 0
+    rng = np.random.default_rng(23)
+    g = (rng.normal(size=(len(o), 3)) * ok[:, None]).astype(np.float32)
+    gd = (rng.uniform(0.0, 1.0, size=len(o)) * ok).astype(np.float32)
+    scene = api.Scene.from_workload(sc)
+    to, td, tg, tgd = to_dev(o, d, g, gd)
+    res = torch.empty(len(o), 3, device=DEV)
+    dist = torch.empty(len(o), 3, device=DEV)
+    rgb = api.render_fwd(scene, to, td, P, residual=res, dist=dist)[0]
+    gs, gsig, gt = api.render_bwd(scene, to, td, P, rgb, tg, residual=res, dist=dist, grad_dist=tgd)
+    ogs, ogsig, ogt = O.render_bwd(osc, o, d, g.astype(np.float64), params=oracle_params(base),
+                                   grad_dist=gd.astype(np.float64))
+    grad_close(gsig.cpu().numpy(), ogsig, "sigma")
+    grad_close(gt.cpu().numpy(), ogt, "tex")
+    grad_close(gs.cpu().numpy(), ogs, "sites")
+
+
+def test_distortion_autograd_and_rho(tiny):
+    """Training-style use: sigma = exp(rho) on the GPU, render with the
+    distortion loss, torch autograd through both; equals the explicit calls."""
+    wl, osc, o, d = tiny
+    sc = wl.scene
+    P = gpu_params(wl.params, img_w=64, img_h=64, n_images=1)
+    scene = api.Scene.from_workload(sc)
+    rho = torch.log(torch.tensor(sc.sigma, device=DEV)).requires_grad_(True)
+    sites = torch.tensor(sc.sites, device=DEV, requires_grad=True)
+    tex = torch.tensor(sc.tex, device=DEV, requires_grad=True)
+    sigma = api.SigmaFromRho.apply(rho)
+    assert torch.allclose(sigma, torch.exp(rho.detach()), rtol=2e-7, atol=0)
+    scene.update(sigma=sigma.detach())
+    to, td = to_dev(o, d)
+    Y = torch.as_tensor(W.target_image(len(o), 1), device=DEV)
+    rgb, Ld = api.render(sites, sigma, tex, to, td, scene, P, with_dist=True)
+    lam = 0.01
+    loss = ((rgb - Y) ** 2).mean() + lam * Ld.mean()
+    loss.backward()
+    res = torch.empty(len(o), 3, device=DEV)
+    dist = torch.empty(len(o), 3, device=DEV)
+    rgb2 = api.render_fwd(scene, to, td, P, residual=res, dist=dist)[0]
+    assert torch.equal(rgb2, rgb.detach()) and torch.equal(dist[:, 0], Ld.detach())
+    gd = torch.full((len(o),), lam / len(o), device=DEV)
+    gs, gsig, gt = api.render_bwd(scene, to, td, P, rgb2, 2 * (rgb2 - Y) / rgb2.numel(), residual=res, dist=dist,
+                                  grad_dist=gd)
+    assert torch.allclose(sites.grad, gs, rtol=1e-5, atol=1e-9)
+    assert torch.allclose(tex.grad, gt, rtol=1e-5, atol=1e-9)
+    assert torch.allclose(rho.grad, gsig * sigma.detach(), rtol=1e-5, atol=1e-12)  # Eq. 4
+
+
+def test_distortion_rejects_negative_t_near(tiny):
+    wl, osc, o, d = tiny
+    scene = api.Scene.from_workload(wl.scene)
+    to, td = to_dev(o[:10], d[:10])
+    dist = torch.empty(10, 3, device=DEV)
+    with pytest.raises(api.VTError):
+        api.render_fwd(scene, to, td, gpu_params(wl.params, t_near=-0.5), dist=dist)
+    rgb = api.render_fwd(scene, to, td, gpu_params(wl.params))[0]
+    with pytest.raises(api.VTError):  # grad_dist without the forward's totals
+        api.render_bwd(scene, to, td, gpu_params(wl.params), rgb, torch.zeros_like(rgb),
+                       grad_dist=torch.ones(10, device=DEV))
+
+
+# ---------------------------------------------------------------- FP16 neighbour offsets (Sec. 5.6 inference variant)
+
+def test_half_offsets_forward_against_exact_walk(medium):
+    """FP16 offsets move each plane by about |n| 2^-11, so rays that pass
+    close to a Voronoi edge may take another cell; the rest keep the exact
+    sequence. Reports the mismatch count; bounds it and the image error."""
+    sc, osc, o, d, cams = medium
+    base = W.default_params()
+    P = gpu_params(base, img_w=203, img_h=121, n_images=2)
+    to, td = to_dev(o, d)
+    half = api.Scene.from_workload(sc, half_offsets=True)
+    full = api.Scene.from_workload(sc)
+    rgb_h = api.render_fwd(half, to, td, P)[0].cpu().numpy()
+    rgb_f = api.render_fwd(full, to, td, P)[0].cpu().numpy()
+    ch, _, nh = api.trace_cells(half, to, td, P, max_cells=256)
+    assert half.get_error()[0] == 0
+    orgb, _, _, flags = O.render(osc, o, d, params=oracle_params(base))
+    oc, _, on, _ = O.trace(osc, o, d, max_cells=256, params=oracle_params(base))
+    ok = (flags & O.BAND_FLAGS) == 0
+    same = (nh.cpu().numpy() == on) & np.all(ch.cpu().numpy() == oc, axis=1)
+    frac = same[ok].mean()
+    rmse_h = float(np.sqrt(np.mean((rgb_h - orgb) ** 2)))
+    rmse_f = float(np.sqrt(np.mean((rgb_f[ok] - orgb[ok]) ** 2)))
+    print(f"half offsets: {int((~same & ok).sum())} / {int(ok.sum())} unflagged sequences differ; "
+          f"image RMSE {rmse_h:.3g} (exact offsets {rmse_f:.3g})")
+    assert frac >= 0.9 and rmse_h <= 5e-3
+    # forward only
+    with pytest.raises(api.VTError):
+        api.render_bwd(half, to, td, P, torch.as_tensor(rgb_h, device=DEV), torch.zeros(len(o), 3, device=DEV))
+    with pytest.raises(api.VTError):
+        api.render_fwd(half, to, td, P, dist=torch.empty(len(o), 3, device=DEV))

@@ -1,7 +1,7 @@
 """Full-size parity at the benchmark's scale and launch configuration:
 3,000,000 surface-concentrated sites, 8x8 textures, four 1280x832 views
 (4,259,840 rays in one launch, image layout, 4x8 tiles), FP32 and FP16
-texture storage. The oracle computes a strided sample of the rays one by one
+texture storage, and the paper's appearance model with the distortion loss. The oracle computes a strided sample of the rays one by one
 (every 997th ray); gradients are compared for a launch over all rays in which
 only the sampled rays carry dL/dC. Ray generation of the 16 mixed cameras
 (pinhole, fisheye, rolling shutter, thin lens: 29,818,880 rays) is compared
@@ -82,6 +82,53 @@ def test_fullsize_forward_and_backward(big, dtype):
     touched = np.nonzero(np.abs(ogt).reshape(len(ogt), -1).max(1) > 0)[0]
     grad_close(gt.cpu().numpy()[touched], ogt[touched], "tex")
     assert np.abs(gt.cpu().numpy()).reshape(len(ogt), -1).max(1)[np.setdiff1d(np.arange(len(ogt)), touched)].max() == 0
+
+
+def test_fullsize_paper_appearance_with_distortion(big):
+    """The paper's appearance model (Sec. 5.1-5.2) and the distortion loss
+    (Eq. 2) fused into the same full-size launch (FP16 textures), sampled
+    rays against the oracle: colour, L_dist, and the gradients of
+    L = sum g.C + sum gd L_dist."""
+    wl, o, d, sel = big
+    sc = wl.scene
+    c0 = wl.cameras[0]
+    rng = np.random.default_rng(5000 + wl.seed)
+    tvd = rng.normal(0.0, 0.5, size=sc.tex.shape).astype(np.float32)
+    tvi = rng.normal(0.0, 1.5, size=sc.tex.shape).astype(np.float32)
+    P = api.make_params(**wl.params, img_w=c0.w, img_h=c0.h, n_images=len(wl.cameras), appearance=1)
+    scene = api.Scene(sc.sites, sc.sigma, tvi, sc.offsets, sc.indices, tex_dtype="f16", tex_vd=tvd)
+    to = torch.as_tensor(o, device="cuda")
+    td = torch.as_tensor(d, device="cuda")
+    res = torch.empty(len(o), 3, device="cuda")
+    dist = torch.empty(len(o), 3, device="cuda")
+    rgb, _, _ = api.render_fwd(scene, to, td, P, residual=res, dist=dist)
+    assert scene.get_error()[0] == 0
+    q = lambda x: torch.as_tensor(x).half().float().numpy()  # noqa: E731
+    osc = O.OracleScene(sc.sites, sc.sigma, q(tvi), sc.offsets, sc.indices, tex_vd=q(tvd))
+    op = O.make_params(**wl.params, appearance=1)
+    orgb, _, _, flags = O.render(osc, o[sel], d[sel], params=op)
+    ok = (flags & O.BAND_FLAGS) == 0
+    assert ok.mean() > 0.95
+    assert np.abs(rgb.cpu().numpy()[sel][ok] - orgb[ok]).max() <= IMG_TOL
+    L = O.distortion(osc, o[sel], d[sel], params=op)
+    got = dist[:, 0].cpu().numpy()[sel].astype(np.float64)
+    assert np.all(np.abs(got - L)[ok] <= 2e-5 * np.maximum(L, 1e-3 * L.max())[ok])
+    g = np.zeros((len(o), 3), np.float32)
+    gd = np.zeros(len(o), np.float32)
+    g[sel[ok]] = rng.normal(size=(ok.sum(), 3))
+    gd[sel[ok]] = rng.uniform(0.5, 2.0, size=ok.sum())
+    gvd = torch.empty(sc.n, sc.R, sc.R, 3, device="cuda")
+    gs, gsig, gt = api.render_bwd(scene, to, td, P, rgb, torch.as_tensor(g, device="cuda"), residual=res,
+                                  dist=dist, grad_dist=torch.as_tensor(gd, device="cuda"), tex_vd_out=gvd)
+    assert scene.get_error()[0] == 0
+    ogs, ogsig, ogt, ogvd = O.render_bwd(osc, o[sel], d[sel], g[sel].astype(np.float64), params=op,
+                                         grad_dist=gd[sel].astype(np.float64))
+    grad_close(gsig.cpu().numpy(), ogsig, "sigma")
+    grad_close(gs.cpu().numpy(), ogs, "sites")
+    touched = np.nonzero(np.abs(ogt).reshape(len(ogt), -1).max(1) > 0)[0]
+    grad_close(gt.cpu().numpy()[touched], ogt[touched], "tex")
+    touched = np.nonzero(np.abs(ogvd).reshape(len(ogvd), -1).max(1) > 0)[0]
+    grad_close(gvd.cpu().numpy()[touched], ogvd[touched], "tex_vd")
 
 
 def test_fullsize_mixed_camera_raygen():

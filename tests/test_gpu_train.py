@@ -1,0 +1,118 @@
+"""GPU checks of the training step (Sec. 5.3-5.5, Eq. 5): the helper kernels
+against the plain float64 definitions in oracle/training.py, and a short
+multi-view optimisation with Delaunay refreshes that must reduce the loss."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from oracle import training as TR  # noqa: E402
+from paper_2608_17682_gb300 import _vt, api  # noqa: E402
+from paper_2608_17682_gb300 import train as T  # noqa: E402
+
+DEV = "cuda"
+
+
+def _st():
+    return api._stream()
+
+
+@pytest.mark.parametrize("n_pool,n", [(10_000, 777), (4096, 4096), (1_000_003, 65_536)])
+def test_sample_rays_matches_definition(n_pool, n):
+    g = torch.Generator().manual_seed(n)
+    o = torch.rand(n_pool, 3, generator=g).to(DEV)
+    d = torch.rand(n_pool, 3, generator=g).to(DEV)
+    y = torch.rand(n_pool, 3, generator=g).to(DEV)
+    oo, dd, yy = (torch.empty(n, 3, device=DEV) for _ in range(3))
+    idx = torch.empty(n, dtype=torch.int64, device=DEV)
+    _vt.vt_sample_rays(n_pool, o.data_ptr(), d.data_ptr(), y.data_ptr(), n, 99, oo.data_ptr(), dd.data_ptr(),
+                       yy.data_ptr(), idx.data_ptr(), _st())
+    ref = TR.stratified_indices(n_pool, n, 99)
+    assert np.array_equal(idx.cpu().numpy(), ref)
+    r = torch.as_tensor(ref, device=DEV)
+    assert torch.equal(oo, o[r]) and torch.equal(dd, d[r]) and torch.equal(yy, y[r])
+
+
+def test_smooth_l1_kernel():
+    rng = np.random.default_rng(41)
+    a = rng.uniform(0, 1, size=(70_001, 3)).astype(np.float32)
+    b = rng.uniform(0, 1, size=(70_001, 3)).astype(np.float32)
+    ta, tb = torch.as_tensor(a, device=DEV), torch.as_tensor(b, device=DEV)
+    g = torch.empty_like(ta)
+    loss = torch.empty(1, device=DEV)
+    _vt.vt_smooth_l1_loss(len(a), ta.data_ptr(), tb.data_ptr(), 0.05, g.data_ptr(), loss.data_ptr(), _st())
+    L, gr = TR.smooth_l1(a, b, 0.05)
+    assert abs(loss.item() - L) <= 1e-6 * L
+    assert np.allclose(g.cpu().numpy(), gr, rtol=2e-6, atol=1e-13)
+
+
+@pytest.mark.parametrize("R", [4, 8])
+def test_texture_regularizer_kernel(R):
+    rng = np.random.default_rng(42 + R)
+    n = 3001
+    t = rng.normal(size=(n, R, R, 3)).astype(np.float32)
+    v = rng.normal(size=(n, R, R, 3)).astype(np.float32)
+    g0 = (1e-6 * rng.normal(size=(n, R, R, 3))).astype(np.float32)  # small enough that the sum keeps the term
+    tt, tv = torch.as_tensor(t, device=DEV), torch.as_tensor(v, device=DEV)
+    gt, gv = torch.as_tensor(g0, device=DEV).clone(), torch.as_tensor(g0, device=DEV).clone()
+    loss = torch.empty(1, device=DEV)
+    _vt.vt_texture_regularizers(n, R, tt.data_ptr(), tv.data_ptr(), 0.01, 0.005, gt.data_ptr(), gv.data_ptr(),
+                                loss.data_ptr(), _st())
+    L, rgt, rgv = TR.texture_regularizers(t, v, 0.01, 0.005)
+    assert abs(loss.item() - L) <= 1e-5 * L
+    # gradients are added to what the buffers held
+    assert np.allclose(gt.cpu().numpy().astype(np.float64) - g0, rgt, rtol=1e-4, atol=1e-12)
+    assert np.allclose(gv.cpu().numpy().astype(np.float64) - g0, rgv, rtol=1e-4, atol=1e-12)
+
+
+def test_adam_kernel():
+    rng = np.random.default_rng(43)
+    n = 100_003
+    p = rng.normal(size=n).astype(np.float32)
+    tp = torch.as_tensor(p, device=DEV).clone()
+    tm, tv = torch.zeros(n, device=DEV), torch.zeros(n, device=DEV)
+    rp, rm, rv = p.astype(np.float64), np.zeros(n), np.zeros(n)
+    for k in range(1, 5):
+        g = rng.normal(size=n).astype(np.float32)
+        tg = torch.as_tensor(g, device=DEV)
+        _vt.vt_adam_step(n, tp.data_ptr(), tg.data_ptr(), tm.data_ptr(), tv.data_ptr(), 1e-2, 0.9, 0.999, 1e-15, k,
+                         _st())
+        rp, rm, rv = TR.adam(rp, g, rm, rv, 1e-2, 0.9, 0.999, 1e-15, k)
+    assert np.abs(tp.cpu().numpy() - rp).max() <= 2e-6
+
+
+def test_learning_rate_schedules():
+    cfg = T.TrainConfig(iters=20_000)
+    a = T.learning_rates(cfg, 0)
+    assert abs(a["sites"] - 2e-4) < 1e-12 and abs(a["tex"] - 2e-2) < 1e-12
+    assert a["tex_vd"] == 0.0  # quadratic ramp starts at zero
+    assert abs(T.learning_rates(cfg, 999)["rho"] - 0.05) < 1e-12  # linear warm-up over 2,000 iterations
+    assert abs(T.learning_rates(cfg, 2000)["rho"] - 0.1) < 1e-12
+    assert abs(T.learning_rates(cfg, 4000)["tex_vd"] - T.learning_rates(cfg, 4000)["tex"]) < 1e-15
+    assert T.learning_rates(cfg, 18_000)["sites"] == 0.0  # sites fixed for the last 2,000 iterations
+    assert abs(T.learning_rates(cfg, 19_999)["tex"] - 5e-4) < 1e-6
+
+
+def test_training_reduces_loss_with_delaunay_refresh():
+    init, cams, images, rp, gt = T.synthetic_problem(n_sites=4000, n_cams=6, w=64, h=48, tex_res=4, seed=3)
+    cfg = T.TrainConfig(iters=120, rays_per_iter=8192, refresh_every=40, vd_ramp_frac=0.0, seed=1)
+    tr = T.Trainer(init["sites"], init["rho"], init["tex"], init["tex_vd"], cams, images, rp, cfg)
+
+    def image_mse():
+        return float(((tr.render(cams) - images) ** 2).mean().item())
+
+    m0 = image_mse()
+    losses = []
+    for _ in range(cfg.iters):
+        losses.append(tr.step(sync_loss=True)[0])
+    st, _ = tr.scene.get_error()
+    assert st == 0
+    assert tr.refreshes == 2
+    m1 = image_mse()
+    assert np.mean(losses[-10:]) < 0.5 * np.mean(losses[:10]), (losses[:10], losses[-10:])
+    assert m1 < 0.5 * m0, (m0, m1)
+    assert torch.isfinite(tr.p["sites"]).all() and torch.isfinite(tr.p["rho"]).all()

@@ -65,7 +65,13 @@ def test_host_argument_validation(vt):
     assert vt.lib.vt_generate_rays(arr, 1, C.c_void_p(8), C.c_void_p(8), None, None) == vt.VT_ERR_INVALID_ARG
     cam.lens_samples = 4
     assert vt.vt_camera_n_rays(cam) == 64
-    assert vt.lib.vt_render_fwd(None, 1, None, None, None, None, None, None, None, None, None) == vt.VT_ERR_INVALID_ARG
+    assert vt.lib.vt_render_fwd(None, 1, None, None, None, None, None, None, None, None, None,
+                                None) == vt.VT_ERR_INVALID_ARG
+    assert vt.lib.vt_sigma_from_rho(-1, None, None, None) == vt.VT_ERR_INVALID_ARG
+    assert vt.lib.vt_sigma_from_rho_bwd(3, None, None, None, None) == vt.VT_ERR_INVALID_ARG
+    cam.kind, cam.lens_samples = 4, 0  # motion blur needs >= 1 time sample
+    arr = (vt.vt_camera * 1)(cam)
+    assert vt.lib.vt_generate_rays(arr, 1, C.c_void_p(8), C.c_void_p(8), None, None) == vt.VT_ERR_INVALID_ARG
     assert vt.lib.vt_l2_loss(-1, None, None, None, None, None) == vt.VT_ERR_INVALID_ARG
     assert vt.lib.vt_average_samples(4, 0, None, None, None) == vt.VT_ERR_INVALID_ARG
 

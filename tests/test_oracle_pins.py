@@ -1016,3 +1016,78 @@ def test_exp_density_gradient_is_size_invariant():
         assert abs(grho - (g @ (c - bg)) * (1 - alpha) * math.log(1 / (1 - alpha))) < 1e-14
     assert abs(out[0][1] - out[1][1]) < 1e-14
     assert abs(out[0][0] / out[1][0] - 0.1 / 2.0) < 1e-12
+
+
+# ---------------------------------------------------------------- training-step helpers (Eq. 5, appendix)
+
+def test_smooth_l1_matches_library():
+    import torch
+    from oracle import training as TR
+    rng = np.random.default_rng(31)
+    a, b = rng.uniform(0, 1, size=(500, 3)), rng.uniform(0, 1, size=(500, 3))
+    for beta in (1e-2, 0.1, 1.0):
+        L, g = TR.smooth_l1(a, b, beta)
+        ta = torch.tensor(a, requires_grad=True)
+        tl = torch.nn.functional.smooth_l1_loss(ta, torch.tensor(b), beta=beta)
+        tl.backward()
+        assert abs(L - tl.item()) < 1e-15 and np.allclose(g, ta.grad.numpy(), atol=1e-18, rtol=1e-12)
+
+
+def test_adam_matches_library():
+    import torch
+    from oracle import training as TR
+    rng = np.random.default_rng(32)
+    p0 = rng.normal(size=40)
+    gs = [rng.normal(size=40) for _ in range(4)]
+    tp = torch.tensor(p0, requires_grad=True)
+    opt = torch.optim.Adam([tp], lr=3e-2, betas=(0.9, 0.999), eps=1e-8)
+    p, m, v = p0.copy(), np.zeros(40), np.zeros(40)
+    for k, g in enumerate(gs, 1):
+        opt.zero_grad()
+        tp.grad = torch.tensor(g)
+        opt.step()
+        p, m, v = TR.adam(p, g, m, v, 3e-2, 0.9, 0.999, 1e-8, k)
+    assert np.allclose(p, tp.detach().numpy(), rtol=0, atol=1e-14)
+
+
+def test_texture_regularizers_closed_forms_and_fd():
+    from oracle import training as TR
+    rng = np.random.default_rng(33)
+    n, R = 5, 4
+    # constant texture per cell: no deviation from the mean
+    const = np.repeat(np.repeat(rng.normal(size=(n, 1, 1, 3)), R, 1), R, 2)
+    L, gt, gv = TR.texture_regularizers(const, np.zeros_like(const), 1.0, 1.0)
+    assert L < 1e-28 and np.abs(gt).max() < 1e-15 and not gv.any()  # zero up to the rounding of the mean
+    # view-dependent map of constant c: L_vd = 3 c^2 (per texel, averaged over cells and texels)
+    L, _, _ = TR.texture_regularizers(const, np.full_like(const, 0.3), 1.0, 0.0)
+    assert abs(L - 3 * 0.09) < 1e-15
+    # one texel raised by h in one channel of one cell: L_mean = h^2 (1 - 1/R^2) / (N R^2)
+    t = np.zeros((n, R, R, 3))
+    t[2, 1, 3, 0] = 0.7
+    L, _, _ = TR.texture_regularizers(t, np.zeros_like(t), 0.0, 1.0)
+    assert abs(L - 0.49 * (1 - 1 / R ** 2) / (n * R * R)) < 1e-15
+    # gradients by central differences
+    t = rng.normal(size=(n, R, R, 3))
+    v = rng.normal(size=(n, R, R, 3))
+    L, gt, gv = TR.texture_regularizers(t, v, 0.3, 0.7)
+    for _ in range(12):
+        q = tuple(rng.integers(0, s) for s in t.shape)
+        for arr, g in ((t, gt), (v, gv)):
+            h = 1e-6
+            arr[q] += h
+            lp = TR.texture_regularizers(t, v, 0.3, 0.7)[0]
+            arr[q] -= 2 * h
+            lm = TR.texture_regularizers(t, v, 0.3, 0.7)[0]
+            arr[q] += h
+            assert abs((lp - lm) / (2 * h) - g[q]) < 1e-9
+
+
+def test_stratified_ray_sampling():
+    from oracle import training as TR
+    idx = TR.stratified_indices(10_000, 777, seed=5)
+    stride = 10_000 / 777
+    k = np.arange(777)
+    assert np.all(idx >= np.floor(k * stride)) and np.all(idx < np.ceil((k + 1) * stride))
+    assert np.all(np.diff(idx) > 0)
+    # position inside the stratum is uniform: mean ~ 1/2
+    assert abs(np.mean((idx + 0.5) / stride - k) - 0.5) < 0.05
