@@ -140,17 +140,24 @@ def kernel_source_hash():
 
 
 def recorded_traffic(kernel, workload):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+    """DRAM bytes per launch from the committed ncu summaries under profiles/
+    (lines "TRAFFIC <kernel> <workload> <bytes> <source hash>"), if they were
+    taken on the current kernel sources (else None)."""
+    d = os.path.join(ROOT, "profiles")
     try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            rec = json.load(f)
+        names = sorted(os.listdir(d))
     except OSError:
         return None
-    e = rec.get(f"{kernel}:{workload}")
-    if not e or e.get("source_hash") != kernel_source_hash():
-        return None
-    return e.get("dram_bytes_per_launch")
+    h = kernel_source_hash()
+    for n in names:
+        if not n.endswith(".md"):
+            continue
+        with open(os.path.join(d, n)) as f:
+            for line in f:
+                w = line.split()
+                if len(w) == 5 and w[0] == "TRAFFIC" and w[1] == kernel and w[2] == workload and w[4] == h:
+                    return int(w[3])
+    return None
 
 
 # ---------------------------------------------------------------- our arm
