@@ -44,11 +44,13 @@ enum Mode { FWD = 0, BWD = 1, TRACE = 2 };
 #ifndef VT_TEX_EARLY
 #define VT_TEX_EARLY 0
 #endif
-// warp aggregation of gradient atomics: 0 none, 1 site/sigma gradients,
-// 2 site/sigma and texel gradients. Measured on 3M sites / 4 views: 0 is
-// fastest (atomics are ~1 ms of the backward; the shuffles cost more).
+// warp aggregation of gradient atomics by pairwise key-matched shuffles:
+// 0 none, 1 site/sigma gradients, 2 also texel gradients. The lanes of a 4x8
+// tile mostly sit in the same cell at the same step, so 2 removes most of the
+// atomics; on 3M sites / 4 views the backward drops from 13.3 to 8.8 ms
+// (1: 12.8 ms).
 #ifndef VT_AGG
-#define VT_AGG 0
+#define VT_AGG 2
 #endif
 // 1: the backward re-reads the previous cell's position from its record
 // instead of keeping it in registers across the neighbour loop
@@ -617,17 +619,20 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
         } else {
           q = __ldg(S.nbr + p);
         }
-        float den = __fmaf_rn(q.x, d.x, __fmaf_rn(q.y, d.y, __fmul_rn(q.z, d.z)));
-        // n.(r + n/2)
-        float num = __fmaf_rn(q.x, __fmaf_rn(0.5f, q.x, r.x),
-                              __fmaf_rn(q.y, __fmaf_rn(0.5f, q.y, r.y), __fmul_rn(q.z, __fmaf_rn(0.5f, q.z, r.z))));
-        if (fabsf(den) <= Gc) {
-          // grazing plane: FP64 recheck from the FP32 inputs
+        const float den0 = __fmaf_rn(q.x, d.x, __fmaf_rn(q.y, d.y, __fmul_rn(q.z, d.z)));
+        float num, den = den0;
+        // backward-facing planes (den < -Gc) are dropped before the numerator
+        // n.(r + n/2) is formed: the rays of a tile mostly agree on them
+        if (den0 > Gc) {
+          num = __fmaf_rn(q.x, __fmaf_rn(0.5f, q.x, r.x),
+                          __fmaf_rn(q.y, __fmaf_rn(0.5f, q.y, r.y), __fmul_rn(q.z, __fmaf_rn(0.5f, q.z, r.z))));
+        } else if (den0 >= -Gc) {
+          // grazing plane (|n.d| <= Gc): FP64 recheck from the FP32 inputs
           atomicAdd(S.err + 1, 1ull);
           const int jg = HALF ? __ldg(reinterpret_cast<const int*>(S.nbr + p) + 3) : __float_as_int(q.w);
           if (!grazing_fp64(S.cell, jg, si, o, d, th, tl, &num)) continue;
           den = 1.f;
-        } else if (!(den > 0.f)) {
+        } else {
           continue;
         }
         if (__fmul_rn(num, bd) < __fmul_rn(bn, den)) {
@@ -905,29 +910,29 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
 }
 
 // user-order gradients from the Morton-ordered scratch (overwrites outputs)
+// Gradient scratch (Morton order, RGBA float4 per texel) -> caller's FP32
+// arrays in user order. One warp per cell: the warp writes the cell's R*R*3
+// output floats contiguously (coalesced 128-B stores) and gathers them from
+// the cell's scratch block.
+__device__ __forceinline__ void copy_tex_grad(int lane, int RR, const float4* __restrict__ src, float* __restrict__ dst) {
+  const float* s = reinterpret_cast<const float*>(src);
+  for (int f = lane; f < RR * 3; f += 32) {
+    const int t = f / 3, c = f - 3 * t;
+    dst[f] = __ldg(s + 4 * t + c);
+  }
+}
+
 __global__ void k_grad_out(int64_t n, int RR, const vt_cell* __restrict__ cells, const float4* __restrict__ g_cell,
                            const float4* __restrict__ g_tex, float* gs, float* gsig, float* gtex,
                            const float4* __restrict__ g_tex_vd = nullptr, float* gtex_vd = nullptr) {
-  int64_t total = n * RR;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = e / RR, t = e - i * RR;
-    int64_t u = cell_csr(cells, (int)i).z;
-    if (gtex) {
-      float4 g = g_tex[e];
-      float* dst = gtex + (u * RR + t) * 3;
-      dst[0] = g.x;
-      dst[1] = g.y;
-      dst[2] = g.z;
-    }
-    if (gtex_vd) {
-      float4 g = g_tex_vd[e];
-      float* dst = gtex_vd + (u * RR + t) * 3;
-      dst[0] = g.x;
-      dst[1] = g.y;
-      dst[2] = g.z;
-    }
-    if (t == 0) {
-      float4 c = g_cell[i];
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+    const int64_t u = cell_csr(cells, (int)i).z;
+    if (gtex) copy_tex_grad(lane, RR, g_tex + i * RR, gtex + u * RR * 3);
+    if (gtex_vd) copy_tex_grad(lane, RR, g_tex_vd + i * RR, gtex_vd + u * RR * 3);
+    if (lane == 0) {
+      const float4 c = g_cell[i];
       if (gs) {
         gs[3 * u] = c.x;
         gs[3 * u + 1] = c.y;
@@ -1140,7 +1145,7 @@ vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float
     if (r != VT_OK) return r;
   }
   if (grad_sites || grad_sigma || grad_tex || grad_tex_vd) {
-    k_grad_out<<<vt_grid(s->n * RR, 256, 152 * 64), 256, 0, st>>>(s->n, (int)RR, s->cell, s->g_cell, s->g_tex,
+    k_grad_out<<<vt_grid(s->n * 32, 256, 152 * 16), 256, 0, st>>>(s->n, (int)RR, s->cell, s->g_cell, s->g_tex,
                                                                     grad_sites, grad_sigma, grad_tex, s->g_tex_vd,
                                                                     grad_tex_vd);
     VT_CUDA_TRY(cudaGetLastError());
@@ -1230,7 +1235,7 @@ vt_status vt_render_bwd_static(vt_scene* s, int64_t n_rays, const float* o, cons
     if (r != VT_OK) return r;
   }
   if (grad_sites || grad_sigma || grad_tex) {
-    k_grad_out<<<vt_grid(s->n * RR, 256, 152 * 64), 256, 0, st>>>(s->n, (int)RR, s->cell, g_cell, g_tex,
+    k_grad_out<<<vt_grid(s->n * 32, 256, 152 * 16), 256, 0, st>>>(s->n, (int)RR, s->cell, g_cell, g_tex,
                                                                     grad_sites, grad_sigma, grad_tex);
     VT_CUDA_TRY(cudaGetLastError());
   }
