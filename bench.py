@@ -207,11 +207,20 @@ def run_ours(args, ws, rank, local):
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
+    def walk_events(pair):
+        """Make the library record `pair` around its next walk kernel."""
+        params.walk_events[0] = pair[0].cuda_event if pair else None
+        params.walk_events[1] = pair[1].cuda_event if pair else None
+
     def step(scene, marks=None, fwd_only=False):
+        # marks: 4 events around the fwd / bwd calls, then 4 the library
+        # records around the forward and backward walk kernels themselves
         api.generate_rays(cams, out=(o, d, tm))
         if marks:
             marks[0].record(stream)
+            walk_events(marks[4:6])
         api.render_fwd(scene, o, d, params, time=tm, out=(rgb, T, steps), residual=None if fwd_only else res)
+        walk_events(None)
         if marks:
             marks[1].record(stream)
         if fwd_only:
@@ -219,7 +228,9 @@ def run_ours(args, ws, rank, local):
         loss, grad = api.l2_loss(rgb, Y)
         if marks:
             marks[2].record(stream)
+            walk_events(marks[6:8])
         api.render_bwd(scene, o, d, params, rgb, grad, time=tm, out=(gs, gsig, gt), residual=res)
+        walk_events(None)
         if marks:
             marks[3].record(stream)
         return loss
@@ -230,8 +241,10 @@ def run_ours(args, ws, rank, local):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def timed(scene, K, fwd_only=False):
-        """K steps, L2 flushed between steps (outside the timed events)."""
+    def timed(scene, K, fwd_only=False, walks=None):
+        """K steps, L2 flushed between steps (outside the timed events). If
+        `walks` is a dict it receives the mean forward / backward walk-kernel
+        times (events recorded by the library around the kernel launches)."""
         for _ in range(args.warmup):
             step(scene, fwd_only=fwd_only)
         barrier()
@@ -239,7 +252,9 @@ def run_ours(args, ws, rank, local):
         for _ in range(K):
             flush.zero_()
             a, b = ev(), ev()
-            m = [ev() for _ in range(4)]
+            m = [ev() for _ in range(8)]
+            for e in m[4:]:
+                e.record(stream)  # creates the event handle the library records into
             a.record(stream)
             step(scene, m, fwd_only=fwd_only)
             b.record(stream)
@@ -250,12 +265,16 @@ def run_ours(args, ws, rank, local):
         total = sum(x.elapsed_time(y) for x, y in zip(st, en))
         fwd = sum(m[0].elapsed_time(m[1]) for m in marks) / K
         bwd = 0.0 if fwd_only else sum(m[2].elapsed_time(m[3]) for m in marks) / K
+        if walks is not None:
+            walks["fwd"] = sum(m[4].elapsed_time(m[5]) for m in marks) / K
+            walks["bwd"] = 0.0 if fwd_only else sum(m[6].elapsed_time(m[7]) for m in marks) / K
         return total / K, fwd, bwd
 
     main = scenes[args.tex]
     clocks = ClockSampler(local)
     clocks.start()
-    ms_step, ms_fwd, ms_bwd = timed(main, args.steps)
+    walks = {}
+    ms_step, ms_fwd, ms_bwd = timed(main, args.steps, walks=walks)
     clk = clocks.stop()
     # the max over ranks
     if ws > 1:
@@ -455,8 +474,8 @@ def run_ours(args, ws, rank, local):
     b_fwd_step = 32 + 16 * E / N + 4 * tb  # cell record + neighbour plane records + 4 texels
     b_bwd_step = b_fwd_step + 2 * (16 + 4 * 16)  # + RMW of one cell and four texel gradient float4s
     io_fwd, io_bwd = 24 + 20, 24 + 24
-    dom = "bwd" if ms_bwd >= ms_fwd else "fwd"
-    ms_dom = ms_bwd if dom == "bwd" else ms_fwd
+    dom = "bwd" if walks["bwd"] >= walks["fwd"] else "fwd"
+    ms_dom = walks[dom]  # the walk kernel alone (library-recorded events)
     alg = sum_steps * (b_bwd_step if dom == "bwd" else b_fwd_step) + n_rays * (io_bwd if dom == "bwd" else io_fwd)
     achieved = alg / (ms_dom * 1e-3) / 1e9
     peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
@@ -477,6 +496,7 @@ def run_ours(args, ws, rank, local):
                    "l2": "flushed between timed steps (256 MB write outside the timed events)",
                    "scene_bytes": int(N * 32 + E * 16 + N * R * R * tb)},
         "ms_fwd": round(ms_fwd, 4), "ms_bwd": round(ms_bwd, 4),
+        "ms_walk_kernel": {"fwd": round(walks["fwd"], 4), "bwd": round(walks["bwd"], 4)},
         "fps_fwd_bwd": round(n_img / (ms_step * 1e-3), 2),
         "mean_cells_per_ray": round(sum_steps / n_rays, 3), "fp64_rechecks_per_step": fp64 / max(1, args.steps + args.warmup),
         "clocks": clk, "e2e": e2e, "gpu_launches": 9 * args.steps, "roofline": roof, **extra,

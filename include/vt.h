@@ -119,6 +119,10 @@ typedef struct {
                               T_vi = tex, T_vd = tex_vd (logits), x = where the ray
                               enters the cell (the cell holding the origin: where it
                               leaves it, or its segment end if it never leaves)      */
+  void* walk_events[2];    /* optional cudaEvent_t pair: recorded on the call's stream
+                              right before and right after the walk kernel of
+                              vt_render_fwd / vt_render_bwd / vt_trace_cells, so a
+                              caller can time that kernel alone. NULL: not recorded */
 } vt_render_params;
 
 /* Fill `p` with the defaults listed above. */

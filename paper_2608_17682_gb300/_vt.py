@@ -47,7 +47,7 @@ class vt_render_params(C.Structure):
                 ("clip_lo", C.c_float * 3), ("clip_hi", C.c_float * 3), ("T_eps", C.c_float),
                 ("skip_weight", C.c_float), ("bg", C.c_float * 3), ("img_w", C.c_int32), ("img_h", C.c_int32),
                 ("n_images", C.c_int32), ("max_steps", C.c_int32), ("image_sizes", C.c_void_p),
-                ("appearance", C.c_int32)]
+                ("appearance", C.c_int32), ("walk_events", C.c_void_p * 2)]
 
 
 class vt_camera(C.Structure):

@@ -1059,8 +1059,8 @@ void launch_walk_app(vt_scene* s, const Scene& S, const RP& P, const float* o, c
 }
 
 template <int MODE>
-vt_status launch_walk(vt_scene* s, const Scene& S, const RP& P, const float* o, const float* d, float* rgb,
-                      float* T, int32_t* steps, Grad G, Trace TR, cudaStream_t st) {
+vt_status launch_walk_kernel(vt_scene* s, const Scene& S, const RP& P, const float* o, const float* d, float* rgb,
+                             float* T, int32_t* steps, Grad G, Trace TR, cudaStream_t st) {
   int64_t nt = walk_threads(P);
   if (nt == 0) return VT_OK;
   int g = vt_grid(nt, 256, ((int64_t)1 << 31) - 1);
@@ -1086,6 +1086,17 @@ vt_status launch_walk(vt_scene* s, const Scene& S, const RP& P, const float* o, 
   return VT_OK;
 }
 
+// the walk launch, bracketed by the caller's timing events if it gave any
+template <int MODE>
+vt_status launch_walk(vt_scene* s, const Scene& S, const RP& P, const float* o, const float* d, float* rgb,
+                      float* T, int32_t* steps, Grad G, Trace TR, cudaStream_t st, const vt_render_params* p) {
+  if (p && p->walk_events[0]) VT_CUDA_TRY(cudaEventRecord((cudaEvent_t)p->walk_events[0], st));
+  vt_status r = launch_walk_kernel<MODE>(s, S, P, o, d, rgb, T, steps, G, TR, st);
+  if (r != VT_OK) return r;
+  if (p && p->walk_events[1]) VT_CUDA_TRY(cudaEventRecord((cudaEvent_t)p->walk_events[1], st));
+  return VT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1108,7 +1119,7 @@ vt_status vt_render_fwd(vt_scene* s, int64_t n_rays, const float* o, const float
   Grad G{};
   G.rgb_lo = rgb_residual;
   G.dist = dist_out;
-  return launch_walk<FWD>(s, S, P, o, d, rgb_out, T_out, steps_out, G, Trace{}, st);
+  return launch_walk<FWD>(s, S, P, o, d, rgb_out, T_out, steps_out, G, Trace{}, st, p);
 }
 
 vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float* d, const float* time,
@@ -1141,7 +1152,7 @@ vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float
       G.dist = const_cast<float*>(dist_out);  // read only in the backward
       G.gdist = grad_dist;
     }
-    r = launch_walk<BWD>(s, S, P, o, d, nullptr, nullptr, nullptr, G, Trace{}, st);
+    r = launch_walk<BWD>(s, S, P, o, d, nullptr, nullptr, nullptr, G, Trace{}, st, p);
     if (r != VT_OK) return r;
   }
   if (grad_sites || grad_sigma || grad_tex || grad_tex_vd) {
@@ -1166,7 +1177,7 @@ vt_status vt_trace_cells(vt_scene* s, int64_t n_rays, const float* o, const floa
   r = anchors(s, S, P, o, st);
   if (r != VT_OK) return r;
   Trace TR{cells, t_exit, n_cells, max_cells};
-  return launch_walk<TRACE>(s, S, P, o, d, nullptr, nullptr, nullptr, Grad{}, TR, st);
+  return launch_walk<TRACE>(s, S, P, o, d, nullptr, nullptr, nullptr, Grad{}, TR, st, p);
 }
 
 // ---------------------------------------------------------------- allocation-free backward
@@ -1231,7 +1242,7 @@ vt_status vt_render_bwd_static(vt_scene* s, int64_t n_rays, const float* o, cons
     r = anchors(s, S, P, o, st);
     if (r != VT_OK) return r;
     Grad G{g_cell, g_tex, nullptr, rgb_out, nullptr, grad_rgb, nullptr, nullptr};
-    r = launch_walk<BWD>(s, S, P, o, d, nullptr, nullptr, nullptr, G, Trace{}, st);
+    r = launch_walk<BWD>(s, S, P, o, d, nullptr, nullptr, nullptr, G, Trace{}, st, p);
     if (r != VT_OK) return r;
   }
   if (grad_sites || grad_sigma || grad_tex) {
