@@ -257,8 +257,11 @@ vt_status vt_render_fwd(vt_scene* s, int64_t n_rays, const float* o, const float
  * gradients include the distortion loss and dist_out must be the forward's
  * dist_out for the same rays (VT_ERR_INVALID_ARG if NULL). Any of the gradient
  * pointers may be NULL to skip that output; grad_tex_vd is for appearance 1.
- * Library-owned scratch (one float4 per cell and per texel) is allocated on
- * first use and kept with the scene. */
+ * Library-owned scratch (one float4 per cell and per texel, one byte per
+ * cell) is allocated on first use and kept with the scene; the call leaves the
+ * texel scratch zeroed for the next one (only the cells this call touched are
+ * rewritten). Backward calls on one scene share that scratch: order them on
+ * one stream. */
 vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float* d, const float* time,
                         const vt_render_params* p, const float* rgb_out, const float* rgb_residual,
                         const float* dist_out, const float* grad_rgb, const float* grad_dist, float* grad_sites,

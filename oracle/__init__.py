@@ -24,8 +24,10 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain C, -O2, pthreads)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", _SRC, "-o", tmp,
-                               "-lm", "-lpthread"])
+        # -ffp-contract=off: no fused multiply-adds, so the arithmetic is the
+        # source's as written, on x86 and Arm alike
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-D_GNU_SOURCE", "-fPIC", "-shared", _SRC,
+                               "-o", tmp, "-lm", "-lpthread"])
         os.replace(tmp, _LIB)
     return _LIB
 

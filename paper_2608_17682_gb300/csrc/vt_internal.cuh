@@ -50,6 +50,11 @@ struct vt_scene {
   float4* g_cell = nullptr;
   float4* g_tex = nullptr;
   float4* g_tex_vd = nullptr;
+  // cells whose texel scratch holds sums (set by the backward walk, cleared
+  // by the gradient permute, which also re-zeroes those cells' scratch);
+  // g_tex_clean: the texel scratch is zero outside the flagged cells
+  uint8_t* g_touched = nullptr;
+  bool g_tex_clean = false;
 };
 
 static inline size_t vt_texel_bytes(int32_t dtype) { return dtype == VT_F32 ? 16 : 8; }

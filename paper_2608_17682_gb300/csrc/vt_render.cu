@@ -113,6 +113,7 @@ struct Grad {
   // the forward, read by the backward; dL/dL_dist per ray (backward)
   float* dist;
   const float* gdist;
+  uint8_t* touched;  // per cell: texel scratch written (null: not tracked)
 };
 
 struct Trace {
@@ -465,7 +466,7 @@ __device__ __forceinline__ void add_cell_grad(float4* g_cell, int c, float gx, f
 
 // texel gradients of the four bilinear taps: g * w * tap weight
 __device__ __forceinline__ void add_tex_grad(float4* g_tex, int64_t b0, int sx, int sy, float g0, float g1, float g2,
-                                             float w, const float (&tw)[4], bool agg) {
+                                             float w, const float (&tw)[4], bool agg, uint8_t* touched, int cell) {
   const float a0 = w * tw[0], a1 = w * tw[1], a2 = w * tw[2], a3 = w * tw[3];
   float v[12] = {g0 * a0, g1 * a0, g2 * a0, g0 * a1, g1 * a1, g2 * a1,
                  g0 * a2, g1 * a2, g2 * a2, g0 * a3, g1 * a3, g2 * a3};
@@ -473,10 +474,14 @@ __device__ __forceinline__ void add_tex_grad(float4* g_tex, int64_t b0, int sx, 
   if (agg) warp_combine<12>(__activemask(), (int)b0, v);
 #endif
   const int64_t e[4] = {b0, b0 + sx, b0 + sy, b0 + sx + sy};
+  bool any = false;
 #pragma unroll
   for (int q = 0; q < 4; ++q)
-    if (v[3 * q] != 0.f || v[3 * q + 1] != 0.f || v[3 * q + 2] != 0.f)
+    if (v[3 * q] != 0.f || v[3 * q + 1] != 0.f || v[3 * q + 2] != 0.f) {
       atomicAdd(g_tex + e[q], make_float4(v[3 * q], v[3 * q + 1], v[3 * q + 2], 0.f));
+      any = true;
+    }
+  if (any && touched) touched[cell] = 1;  // every writer stores the same value
 }
 
 // ---------------------------------------------------------------- the walk
@@ -834,10 +839,13 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
         if (pc >= 0) add_cell_grad(G.g_cell, pc, p_gs.x, p_gs.y, p_gs.z, p_gsig);
         if (coloured && w > 0.f) {
           if constexpr (APP == 0) {
-            add_tex_grad(G.g_tex, tb0, tp.sx, tp.sy, g0, g1, g2, w, tw, S.n * S.RR < ((int64_t)1 << 31));
+            add_tex_grad(G.g_tex, tb0, tp.sx, tp.sy, g0, g1, g2, w, tw, S.n * S.RR < ((int64_t)1 << 31), G.touched,
+                         cell);
           } else {
-            add_tex_grad(G.g_tex, tbv, tv.sx, tv.sy, gz0, gz1, gz2, 1.f, wv, S.n * S.RR < ((int64_t)1 << 31));
-            add_tex_grad(G.g_tex_vd, tb0, tp.sx, tp.sy, gz0, gz1, gz2, 1.f, tw, S.n * S.RR < ((int64_t)1 << 31));
+            add_tex_grad(G.g_tex, tbv, tv.sx, tv.sy, gz0, gz1, gz2, 1.f, wv, S.n * S.RR < ((int64_t)1 << 31), G.touched,
+                         cell);
+            add_tex_grad(G.g_tex_vd, tb0, tp.sx, tp.sy, gz0, gz1, gz2, 1.f, tw, S.n * S.RR < ((int64_t)1 << 31),
+                         G.touched, cell);
           }
         }
         pc = cell;
@@ -913,25 +921,37 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
 // Gradient scratch (Morton order, RGBA float4 per texel) -> caller's FP32
 // arrays in user order. One warp per cell: the warp writes the cell's R*R*3
 // output floats contiguously (coalesced 128-B stores) and gathers them from
-// the cell's scratch block.
-__device__ __forceinline__ void copy_tex_grad(int lane, int RR, const float4* __restrict__ src, float* __restrict__ dst) {
+// the cell's scratch block. With `touched` (the backward walk flags the cells
+// it added texel gradients to), cells not flagged are known to be zero: their
+// outputs are written as zeros without reading the scratch, and the flagged
+// cells' scratch is re-zeroed here, so the next backward needs no clear.
+__device__ __forceinline__ void copy_tex_grad(int lane, int RR, bool hot, float4* __restrict__ src, float* dst,
+                                              bool rezero) {
   const float* s = reinterpret_cast<const float*>(src);
-  for (int f = lane; f < RR * 3; f += 32) {
-    const int t = f / 3, c = f - 3 * t;
-    dst[f] = __ldg(s + 4 * t + c);
+  if (dst)
+    for (int f = lane; f < RR * 3; f += 32) {
+      const int t = f / 3, c = f - 3 * t;
+      dst[f] = hot ? s[4 * t + c] : 0.f;
+    }
+  if (hot && rezero) {
+    __syncwarp();  // every lane has read the block
+    for (int t = lane; t < RR; t += 32) src[t] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 
 __global__ void k_grad_out(int64_t n, int RR, const vt_cell* __restrict__ cells, const float4* __restrict__ g_cell,
-                           const float4* __restrict__ g_tex, float* gs, float* gsig, float* gtex,
-                           const float4* __restrict__ g_tex_vd = nullptr, float* gtex_vd = nullptr) {
+                           float4* g_tex, float* gs, float* gsig, float* gtex, float4* g_tex_vd, float* gtex_vd,
+                           uint8_t* touched) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
     const int64_t u = cell_csr(cells, (int)i).z;
-    if (gtex) copy_tex_grad(lane, RR, g_tex + i * RR, gtex + u * RR * 3);
-    if (gtex_vd) copy_tex_grad(lane, RR, g_tex_vd + i * RR, gtex_vd + u * RR * 3);
+    const bool hot = !touched || touched[i];
+    if (gtex || touched) copy_tex_grad(lane, RR, hot, g_tex + i * RR, gtex ? gtex + u * RR * 3 : nullptr, touched);
+    if (g_tex_vd && (gtex_vd || touched))
+      copy_tex_grad(lane, RR, hot, g_tex_vd + i * RR, gtex_vd ? gtex_vd + u * RR * 3 : nullptr, touched);
     if (lane == 0) {
+      if (touched && hot) touched[i] = 0;
       const float4 c = g_cell[i];
       if (gs) {
         gs[3 * u] = c.x;
@@ -1138,16 +1158,31 @@ vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t RR = (int64_t)s->R * s->R;
   if (!s->g_cell) VT_CUDA_TRY(cudaMalloc(&s->g_cell, s->n * sizeof(float4)));
-  if (!s->g_tex) VT_CUDA_TRY(cudaMalloc(&s->g_tex, s->n * RR * sizeof(float4)));
-  if (s->tex_vd && !s->g_tex_vd) VT_CUDA_TRY(cudaMalloc(&s->g_tex_vd, s->n * RR * sizeof(float4)));
+  if (!s->g_tex) {
+    s->g_tex_clean = false;
+    VT_CUDA_TRY(cudaMalloc(&s->g_tex, s->n * RR * sizeof(float4)));
+  }
+  if (s->tex_vd && !s->g_tex_vd) {
+    s->g_tex_clean = false;
+    VT_CUDA_TRY(cudaMalloc(&s->g_tex_vd, s->n * RR * sizeof(float4)));
+  }
+  if (!s->g_touched) {
+    s->g_tex_clean = false;
+    VT_CUDA_TRY(cudaMalloc(&s->g_touched, s->n));
+  }
   VT_CUDA_TRY(cudaMemsetAsync(s->g_cell, 0, s->n * sizeof(float4), st));
-  VT_CUDA_TRY(cudaMemsetAsync(s->g_tex, 0, s->n * RR * sizeof(float4), st));
-  if (s->g_tex_vd) VT_CUDA_TRY(cudaMemsetAsync(s->g_tex_vd, 0, s->n * RR * sizeof(float4), st));
+  if (!s->g_tex_clean) {
+    // first use, or a previous call stopped before its permute: clear everything
+    VT_CUDA_TRY(cudaMemsetAsync(s->g_tex, 0, s->n * RR * sizeof(float4), st));
+    if (s->g_tex_vd) VT_CUDA_TRY(cudaMemsetAsync(s->g_tex_vd, 0, s->n * RR * sizeof(float4), st));
+    VT_CUDA_TRY(cudaMemsetAsync(s->g_touched, 0, s->n, st));
+  }
+  s->g_tex_clean = false;  // until this call's permute is enqueued
   Scene S = scene_view(s);
   if (n_rays > 0) {
     r = anchors(s, S, P, o, st);
     if (r != VT_OK) return r;
-    Grad G{s->g_cell, s->g_tex, s->g_tex_vd, rgb_out, rgb_residual, grad_rgb, nullptr, nullptr};
+    Grad G{s->g_cell, s->g_tex, s->g_tex_vd, rgb_out, rgb_residual, grad_rgb, nullptr, nullptr, s->g_touched};
     if (grad_dist) {
       G.dist = const_cast<float*>(dist_out);  // read only in the backward
       G.gdist = grad_dist;
@@ -1155,12 +1190,12 @@ vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float
     r = launch_walk<BWD>(s, S, P, o, d, nullptr, nullptr, nullptr, G, Trace{}, st, p);
     if (r != VT_OK) return r;
   }
-  if (grad_sites || grad_sigma || grad_tex || grad_tex_vd) {
-    k_grad_out<<<vt_grid(s->n * 32, 256, 152 * 16), 256, 0, st>>>(s->n, (int)RR, s->cell, s->g_cell, s->g_tex,
-                                                                    grad_sites, grad_sigma, grad_tex, s->g_tex_vd,
-                                                                    grad_tex_vd);
-    VT_CUDA_TRY(cudaGetLastError());
-  }
+  // always launched: it also re-zeroes the flagged cells' texel scratch
+  k_grad_out<<<vt_grid(s->n * 32, 256, 152 * 16), 256, 0, st>>>(s->n, (int)RR, s->cell, s->g_cell, s->g_tex,
+                                                                  grad_sites, grad_sigma, grad_tex, s->g_tex_vd,
+                                                                  grad_tex_vd, s->g_touched);
+  VT_CUDA_TRY(cudaGetLastError());
+  s->g_tex_clean = true;
   return VT_OK;
 }
 
@@ -1241,13 +1276,14 @@ vt_status vt_render_bwd_static(vt_scene* s, int64_t n_rays, const float* o, cons
   if (n_rays > 0) {
     r = anchors(s, S, P, o, st);
     if (r != VT_OK) return r;
-    Grad G{g_cell, g_tex, nullptr, rgb_out, nullptr, grad_rgb, nullptr, nullptr};
+    Grad G{g_cell, g_tex, nullptr, rgb_out, nullptr, grad_rgb, nullptr, nullptr, nullptr};
     r = launch_walk<BWD>(s, S, P, o, d, nullptr, nullptr, nullptr, G, Trace{}, st, p);
     if (r != VT_OK) return r;
   }
   if (grad_sites || grad_sigma || grad_tex) {
     k_grad_out<<<vt_grid(s->n * 32, 256, 152 * 16), 256, 0, st>>>(s->n, (int)RR, s->cell, g_cell, g_tex,
-                                                                    grad_sites, grad_sigma, grad_tex);
+                                                                    grad_sites, grad_sigma, grad_tex, nullptr,
+                                                                    nullptr, nullptr);
     VT_CUDA_TRY(cudaGetLastError());
   }
   return VT_OK;

@@ -298,6 +298,7 @@ void free_scene(vt_scene* s) {
   cudaFree(s->g_cell);
   cudaFree(s->g_tex);
   cudaFree(s->g_tex_vd);
+  cudaFree(s->g_touched);
   delete s;
 }
 

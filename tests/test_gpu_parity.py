@@ -747,3 +747,55 @@ def test_half_offsets_forward_against_exact_walk(medium):
         api.render_bwd(half, to, td, P, torch.as_tensor(rgb_h, device=DEV), torch.zeros(len(o), 3, device=DEV))
     with pytest.raises(api.VTError):
         api.render_fwd(half, to, td, P, dist=torch.empty(len(o), 3, device=DEV))
+
+
+def test_backward_scratch_is_clean_between_calls(medium):
+    """The backward leaves its texel scratch zeroed for the next call (only the
+    cells it touched are rewritten): repeated calls with other rays, other
+    gradients and skipped outputs give the results of a fresh scene."""
+    sc, osc, o, d, cams = medium
+    P = gpu_params(W.default_params())
+    to, td = to_dev(o, d)
+    g = torch.randn(len(o), 3, device=DEV)
+    used = api.Scene.from_workload(sc)
+    rgb = api.render_fwd(used, to, td, P)[0]
+    # dirty the scratch: a call without texel output, then one on half the rays
+    api.render_bwd(used, to, td, P, rgb, g * 3.0, need=(True, True, False))
+    h = len(o) // 2
+    api.render_bwd(used, to[:h].contiguous(), td[:h].contiguous(), P, rgb[:h].contiguous(), g[:h].contiguous())
+    a = api.render_bwd(used, to[h:].contiguous(), td[h:].contiguous(), P, rgb[h:].contiguous(), g[h:].contiguous())
+    fresh = api.Scene.from_workload(sc)
+    b = api.render_bwd(fresh, to[h:].contiguous(), td[h:].contiguous(), P, rgb[h:].contiguous(), g[h:].contiguous())
+    for x, y in zip(a, b):
+        assert (x - y).abs().max().item() <= 1e-5 * max(1.0, y.abs().max().item())
+    # untouched texels are exactly zero
+    touched = b[2].abs().reshape(sc.n, -1).max(1).values > 0
+    assert a[2].reshape(sc.n, -1)[~touched].abs().max().item() == 0.0
+
+
+def test_cuda_path_matches_stored_golden_values():
+    """The CUDA path against the stored oracle values of tests/golden (no
+    oracle run): cells and step counts exact, colours within 1e-4."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_tiny_rays.json")))
+    wl = W.make_workload("tiny")
+    o, d = W.workload_rays(wl)
+    sel = np.array([r["index"] for r in g["rays"]])
+    scene = api.Scene.from_workload(wl.scene)
+    P = gpu_params(wl.params)
+    to, td = to_dev(o[sel], d[sel])
+    dist = torch.empty(len(sel), 3, device=DEV)
+    rgb, T, steps = api.render_fwd(scene, to, td, P, dist=dist)
+    cells, t_exit, n_cells = api.trace_cells(scene, to, td, P, max_cells=64)
+    rgb, T, steps, dist = rgb.cpu().numpy(), T.cpu().numpy(), steps.cpu().numpy(), dist.cpu().numpy()
+    cells, t_exit, n_cells = cells.cpu().numpy(), t_exit.cpu().numpy(), n_cells.cpu().numpy()
+    for k, r in enumerate(g["rays"]):
+        assert r["flags"] == 0
+        n = len(r["cells"])
+        assert steps[k] == r["steps"] and n_cells[k] == n and list(cells[k, :n]) == r["cells"]
+        assert np.abs(rgb[k] - np.array(r["rgb"])).max() <= IMG_TOL and abs(T[k] - r["T"]) <= IMG_TOL
+        assert abs(dist[k, 0] - r["L_dist"]) <= 2e-5 * max(r["L_dist"], 1e-3)
+        te = np.array([np.inf if t is None else t for t in r["t_exit"]])
+        fin = np.isfinite(te)
+        assert np.all(np.abs(t_exit[k, :n][fin] - te[fin]) <= 1e-5 * np.maximum(1.0, np.abs(te[fin])))

@@ -1091,3 +1091,26 @@ def test_stratified_ray_sampling():
     assert np.all(np.diff(idx) > 0)
     # position inside the stratum is uniform: mean ~ 1/2
     assert abs(np.mean((idx + 0.5) / stride - k) - 0.5) < 0.05
+
+
+# ---------------------------------------------------------------- stored expected values
+
+def test_oracle_matches_stored_golden_values():
+    """tests/golden/oracle_tiny_rays.json was written by make_golden.py from
+    the oracle; any change of the oracle's results on these rays shows here."""
+    import json
+    import os
+    import sys
+    sys.path.insert(0, os.path.join(os.path.dirname(__file__), "golden"))
+    import make_golden
+    stored = json.load(open(make_golden.OUT))
+    now = make_golden.compute()
+    assert len(stored["rays"]) == len(now["rays"]) == 36
+    for a, b in zip(stored["rays"], now["rays"]):
+        assert a["cells"] == b["cells"] and a["steps"] == b["steps"] and a["flags"] == b["flags"]
+        assert np.allclose(a["rgb"], b["rgb"], rtol=0, atol=1e-13) and abs(a["T"] - b["T"]) <= 1e-13
+        assert abs(a["L_dist"] - b["L_dist"]) <= 1e-13
+        ta = np.array([np.inf if t is None else t for t in a["t_exit"]])
+        tb = np.array([np.inf if t is None else t for t in b["t_exit"]])
+        assert np.array_equal(np.isinf(ta), np.isinf(tb)) and np.allclose(ta[np.isfinite(ta)], tb[np.isfinite(tb)],
+                                                                             rtol=1e-13, atol=0)
