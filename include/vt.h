@@ -11,14 +11,23 @@
  *   - Sec. 3.2: piecewise-constant volume rendering, alpha_k = 1 -
  *     exp(-sigma_{i_k} delta_k), C = sum_k T_k alpha_k c_k, front to back,
  *     early termination once T falls below a threshold.
- *   - Sec. 5.1: per-cell R x R RGB octahedral texture, bilinear fetch. This
- *     library indexes it at the ray direction d.
+ *   - Sec. 5.1: per-cell R x R RGB octahedral texture, bilinear fetch. By
+ *     default this library indexes it at the ray direction d (appearance 0);
+ *     appearance 1 is the paper's model of Sec. 5.1-5.2 (a surface texture at
+ *     the direction of the entry point from the site plus a view-dependent
+ *     texture at -d, summed as logits, then a sigmoid).
+ *   - Sec. 5.3, Eq. 2: the distortion loss of each ray, computed in the same
+ *     walk (optional output of vt_render_fwd, optional input of vt_render_bwd).
+ *   - Sec. 5.4, Eq. 4: sigma = exp(rho) and its adjoint.
+ *   - Sec. 5.5 / Eq. 5: training-step helpers (ray sampling, Smooth-L1, the
+ *     texture regularisers, Adam).
  *   - Sec. 5.6: RGB texels padded to RGBA for one aligned load, half-precision
  *     appearance storage, Morton-ordered cells, warp-coherent 4x8 ray tiles,
- *     optional low-contribution cell skip.
+ *     optional low-contribution cell skip, optional FP16 neighbour offsets.
  *   - Eq. 3: dL/dsigma = dL/dalpha * delta * (1 - alpha) (the backward pass
  *     computes the same quantity as dL/dtau * delta, tau = sigma*delta).
- *   - Sec. 6.5: camera effects by ray generation only.
+ *   - Sec. 6.5: camera effects by ray generation only (pinhole, equidistant
+ *     fisheye, rolling shutter, thin lens, motion blur).
  *
  * Conventions for every entry point:
  *   - Pointers marked "device" are caller-owned CUDA device pointers (for
