@@ -57,6 +57,13 @@ enum Mode { FWD = 0, BWD = 1, TRACE = 2 };
 #ifndef VT_BWD_RELOAD_PREV
 #define VT_BWD_RELOAD_PREV 1
 #endif
+// tiles per row of the 8-tile patch a 256-thread block renders (8: a 64x4
+// pixel strip; 2: a 16x16 square). On 3M sites / 4 views: 8 327.6, 4 337.5,
+// 1 341.0, 2 346.0 Mrays/s fwd+bwd -- the squarest patch shares the most cells.
+#ifndef VT_ST_W
+#define VT_ST_W 2
+#endif
+constexpr int kPatchH = 8 / VT_ST_W;  // tile rows of a patch
 // unroll factor of the neighbour loop
 #ifndef VT_NBR_UNROLL
 #define VT_NBR_UNROLL 8
@@ -77,7 +84,7 @@ struct Scene {
 // one image of a launch whose images differ in size
 struct ImgEnt {
   int64_t first_ray, first_tile;
-  int w, h, tiles_x, pad;
+  int w, h, tiles_x, st_x;  // st_x: tile patches per row
 };
 
 struct RP {  // render parameters, device copy
@@ -86,7 +93,7 @@ struct RP {  // render parameters, device copy
   float3 lo, hi;
   float T_eps, skip;
   float3 bg;
-  int img_w, img_h, n_images, tiles_x, tiles_per_img;
+  int img_w, img_h, n_images, tiles_x, tiles_per_img, st_x;
   int max_steps;
   int64_t n_rays;
   int64_t anchor_stride;
@@ -421,7 +428,12 @@ __device__ __forceinline__ int64_t ray_of_thread(const RP& P, int64_t tid, int& 
     tiles_x = P.img[lo].tiles_x;
     first = P.img[lo].first_ray;
   }
-  const int ty = (int)(t / tiles_x), tx = (int)(t - (int64_t)ty * tiles_x);
+  // the 8 warps of a block take a VT_ST_W x kPatchH patch of tiles
+  const int st_x = P.layout == 1 ? P.st_x : P.img[img].st_x;
+  const int st = (int)(t >> 3), k = (int)(t & 7);
+  const int sy = st / st_x, sx = st - sy * st_x;
+  const int tx = sx * VT_ST_W + k % VT_ST_W, ty = sy * kPatchH + k / VT_ST_W;
+  if (tx >= tiles_x) return -1;
   const int x = tx * 8 + (lane & 7), y = ty * 4 + (lane >> 3);
   if (x >= w || y >= h) return -1;
   const int64_t ray = first + (int64_t)y * w + x;
@@ -1002,9 +1014,10 @@ vt_status make_rp(const vt_scene* s, int64_t n_rays, const vt_render_params* p, 
       e.w = w;
       e.h = h;
       e.tiles_x = (w + 7) / 8;
-      e.pad = 0;
+      e.st_x = (e.tiles_x + VT_ST_W - 1) / VT_ST_W;
       ray0 += (int64_t)w * h;
-      tile0 += (int64_t)e.tiles_x * ((h + 3) / 4);
+      // warps of this image: 8 per tile patch
+      tile0 += (int64_t)e.st_x * (((h + 3) / 4 + kPatchH - 1) / kPatchH) * 8;
     }
     if (ray0 != n_rays) return VT_ERR_INVALID_ARG;
     P.layout = 2;
@@ -1020,7 +1033,10 @@ vt_status make_rp(const vt_scene* s, int64_t n_rays, const vt_render_params* p, 
     per_image = (int64_t)p->img_w * p->img_h;
     if (per_image * p->n_images != n_rays) return VT_ERR_INVALID_ARG;
     P.tiles_x = (p->img_w + 7) / 8;
-    P.tiles_per_img = P.tiles_x * ((p->img_h + 3) / 4);
+    // warps per image: 8 per patch of VT_ST_W x kPatchH tiles (ragged patches
+    // at the right and bottom edges have idle warps)
+    P.st_x = (P.tiles_x + VT_ST_W - 1) / VT_ST_W;
+    P.tiles_per_img = P.st_x * (((p->img_h + 3) / 4 + kPatchH - 1) / kPatchH) * 8;
     int64_t groups = (p->n_images + VT_MAX_ANCHORS - 1) / VT_MAX_ANCHORS;
     P.anchor_stride = per_image * groups;
   } else {

@@ -799,3 +799,25 @@ def test_cuda_path_matches_stored_golden_values():
         te = np.array([np.inf if t is None else t for t in r["t_exit"]])
         fin = np.isfinite(te)
         assert np.all(np.abs(t_exit[k, :n][fin] - te[fin]) <= 1e-5 * np.maximum(1.0, np.abs(te[fin])))
+
+
+def test_walk_events_time_the_kernel(medium):
+    """vt_render_params.walk_events: the library records the pair around the
+    walk kernel; the interval lies inside the whole call's interval."""
+    sc, osc, o, d, cams = medium
+    P = gpu_params(W.default_params(), img_w=203, img_h=121, n_images=2)
+    to, td = to_dev(o, d)
+    scene = api.Scene.from_workload(sc)
+    st = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for e in ev[1:3]:
+        e.record(st)  # create the handles the library records into
+    torch.cuda.synchronize()
+    P.walk_events[0], P.walk_events[1] = ev[1].cuda_event, ev[2].cuda_event
+    ev[0].record(st)
+    api.render_fwd(scene, to, td, P)
+    ev[3].record(st)
+    torch.cuda.synchronize()
+    walk, call = ev[1].elapsed_time(ev[2]), ev[0].elapsed_time(ev[3])
+    assert 0.0 < walk <= call
+    assert ev[0].elapsed_time(ev[1]) >= 0.0 and ev[2].elapsed_time(ev[3]) >= 0.0
