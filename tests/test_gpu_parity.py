@@ -318,6 +318,11 @@ def test_empty_and_missing_rays(tiny):
     d2 = torch.tensor([[1.0, 0.0, 0.0]] * 5, device=DEV)
     rgb, T, s = api.render_fwd(scene, o2, d2, P)
     assert torch.all(rgb == 1) and torch.all(T == 1) and torch.all(s == 0)
+    # their backward and an empty backward give exactly zero gradients
+    for oo, dd, cc in ((o2, d2, rgb), (e, e, torch.empty(0, 3, device=DEV))):
+        gs, gsig, gt = api.render_bwd(scene, oo, dd, P, cc, torch.ones_like(cc))
+        assert scene.get_error()[0] == 0
+        assert gs.abs().max().item() == 0 and gsig.abs().max().item() == 0 and gt.abs().max().item() == 0
 
 
 def test_single_site_scene_closed_form():
