@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the FP32/BF16 comparison timings")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--appearance", type=int, default=0, choices=[0, 1],
+                    help="1: time the paper's two-texture appearance model as the main step")
     ap.add_argument("--skip-sweep", action="store_true",
                     help="forward-only timing and image change for cell-skip thresholds 0 ... 1e-2")
     ap.add_argument("--ablation", action="store_true",
@@ -184,13 +186,24 @@ def run_ours(args, ws, rank, local):
         layout = dict(img_w=c0.w * spp, img_h=c0.h, n_images=n_img)
     else:  # one launch over images of different sizes (lens samples widen a row)
         layout = dict(image_sizes=[(c.w * c.spp, c.h) for c in cams])
-    params = api.make_params(**wl.params, **layout)
+    params = api.make_params(**wl.params, **layout, appearance=args.appearance)
     Y = torch.as_tensor(W.target_image(n_rays, wl.seed), device=dev)
+
+    # the paper's appearance model (Sec. 5.1-5.2): two maps of logits, sigmoid
+    rng_app = np.random.default_rng(5000 + wl.seed)
+    tvd = rng_app.normal(0.0, 0.5, size=wl.scene.tex.shape).astype(np.float32)
+    tvi = rng_app.normal(0.0, 1.5, size=wl.scene.tex.shape).astype(np.float32)
+
+    def make_scene(t, appearance):
+        if appearance:
+            return api.Scene(wl.scene.sites, wl.scene.sigma, tvi, wl.scene.offsets, wl.scene.indices, tex_dtype=t,
+                             device=dev, tex_vd=tvd)
+        return api.Scene.from_workload(wl.scene, tex_dtype=t, device=dev)
 
     scenes = {}
     dtypes = [args.tex] + ([] if args.no_extra else [t for t in ("f32", "bf16", "f16") if t != args.tex])
     for t in dtypes:
-        scenes[t] = api.Scene.from_workload(wl.scene, tex_dtype=t, device=dev)
+        scenes[t] = make_scene(t, args.appearance)
     stream = torch.cuda.current_stream()
     o = torch.empty(n_rays, 3, device=dev)
     d = torch.empty(n_rays, 3, device=dev)
@@ -297,18 +310,14 @@ def run_ours(args, ws, rank, local):
         extra[t] = {"fwd_bwd_mrays_s": round(n_rays / (m_s * 1e-3) / 1e6 * ws, 2), "ms_fwd": round(m_f, 3),
                     "ms_bwd": round(m_b, 3)}
     if not args.no_extra:
-        # the paper's appearance model (Sec. 5.1-5.2): two maps of logits, sigmoid
-        rng = np.random.default_rng(5000 + wl.seed)
-        tvd = rng.normal(0.0, 0.5, size=wl.scene.tex.shape).astype(np.float32)
-        tvi = rng.normal(0.0, 1.5, size=wl.scene.tex.shape).astype(np.float32)
-        sc_app = api.Scene(wl.scene.sites, wl.scene.sigma, tvi, wl.scene.offsets, wl.scene.indices,
-                           tex_dtype=args.tex, device=dev, tex_vd=tvd)
-        del tvd, tvi
+        # the other appearance model as a comparison line
+        other = 1 - args.appearance
+        sc_app = make_scene(args.tex, other)
         params_main = params
-        params = api.make_params(**wl.params, **layout, appearance=1)
+        params = api.make_params(**wl.params, **layout, appearance=other)
         m_s, m_f, m_b = timed(sc_app, max(3, args.steps // 2))
-        extra["appearance1"] = {"fwd_bwd_mrays_s": round(n_rays / (m_s * 1e-3) / 1e6 * ws, 2),
-                                "ms_fwd": round(m_f, 3), "ms_bwd": round(m_b, 3), "tex": args.tex}
+        extra[f"appearance{other}"] = {"fwd_bwd_mrays_s": round(n_rays / (m_s * 1e-3) / 1e6 * ws, 2),
+                                       "ms_fwd": round(m_f, 3), "ms_bwd": round(m_b, 3), "tex": args.tex}
         params = params_main
         sc_app.close()
         # inference with FP16 neighbour offsets (Sec. 5.6): forward only
@@ -471,8 +480,9 @@ def run_ours(args, ws, rank, local):
     peaks, peak_kind = measured_peaks()
     E = main.n_edges
     tb = 8 if args.tex in ("f16", "bf16") else 16
-    b_fwd_step = 32 + 16 * E / N + 4 * tb  # cell record + neighbour plane records + 4 texels
-    b_bwd_step = b_fwd_step + 2 * (16 + 4 * 16)  # + RMW of one cell and four texel gradient float4s
+    n_tex = 8 if args.appearance else 4  # texels read per coloured cell (two maps for the paper's model)
+    b_fwd_step = 32 + 16 * E / N + n_tex * tb  # cell record + neighbour plane records + texels
+    b_bwd_step = b_fwd_step + 2 * (16 + n_tex * 16)  # + RMW of one cell and the texel gradient float4s
     io_fwd, io_bwd = 24 + 20, 24 + 24
     dom = "bwd" if walks["bwd"] >= walks["fwd"] else "fwd"
     ms_dom = walks[dom]  # the walk kernel alone (library-recorded events)
@@ -486,11 +496,13 @@ def run_ours(args, ws, rank, local):
             "ms_per_launch": round(ms_dom, 4)}
 
     line = {
-        "metric": METRIC if args.tex == "f16" else METRIC.replace("FP16", args.tex.upper()),
+        "metric": (METRIC if args.tex == "f16" else METRIC.replace("FP16", args.tex.upper()))
+        + (", paper appearance model" if args.appearance else ""),
         "value": round(value * 1.0, 3), "unit": "Mrays/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {N} sites, {R}x{R} {args.tex} textures, "
+        "config": {"workload": f"{args.workload}: {N} sites, {R}x{R} {args.tex} textures"
+                               f"{' (two maps, sigmoid)' if args.appearance else ''}, "
                                f"{n_img} x {c0.w}x{c0.h} cameras, {n_rays} rays/GPU",
                    "global_batch": total_rays, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "flushed between timed steps (256 MB write outside the timed events)",
