@@ -194,11 +194,11 @@ def run_ours(args, ws, rank, local):
     tvd = rng_app.normal(0.0, 0.5, size=wl.scene.tex.shape).astype(np.float32)
     tvi = rng_app.normal(0.0, 1.5, size=wl.scene.tex.shape).astype(np.float32)
 
-    def make_scene(t, appearance):
+    def make_scene(t, appearance, **kw):
         if appearance:
             return api.Scene(wl.scene.sites, wl.scene.sigma, tvi, wl.scene.offsets, wl.scene.indices, tex_dtype=t,
-                             device=dev, tex_vd=tvd)
-        return api.Scene.from_workload(wl.scene, tex_dtype=t, device=dev)
+                             device=dev, tex_vd=tvd, **kw)
+        return api.Scene.from_workload(wl.scene, tex_dtype=t, device=dev, **kw)
 
     scenes = {}
     dtypes = [args.tex] + ([] if args.no_extra else [t for t in ("f32", "bf16", "f16") if t != args.tex])
@@ -321,7 +321,7 @@ def run_ours(args, ws, rank, local):
         params = params_main
         sc_app.close()
         # inference with FP16 neighbour offsets (Sec. 5.6): forward only
-        sc_h = api.Scene.from_workload(wl.scene, tex_dtype=args.tex, device=dev, half_offsets=True)
+        sc_h = make_scene(args.tex, args.appearance, half_offsets=True)
         api.generate_rays(cams, out=(o, d, tm))
         api.render_fwd(main, o, d, params, time=tm, out=(rgb, T, steps))
         ref_img = rgb.clone()
@@ -389,9 +389,9 @@ def run_ours(args, ws, rank, local):
 
     if args.ablation:
         # cumulative: user order + row-major 1-D rays -> + Morton -> + 4x8 tiles -> + skip 1e-3
-        base_scene = api.Scene.from_workload(wl.scene, tex_dtype=args.tex, device=dev, keep_order=True)
-        p_1d = api.make_params(**wl.params)
-        p_skip = api.make_params(**{**wl.params, "skip_weight": 1e-3}, **layout)
+        base_scene = make_scene(args.tex, args.appearance, keep_order=True)
+        p_1d = api.make_params(**wl.params, appearance=args.appearance)
+        p_skip = api.make_params(**{**wl.params, "skip_weight": 1e-3}, **layout, appearance=args.appearance)
         rows = []
         for name, sc_, pp in (("base", base_scene, p_1d), ("+morton", main, p_1d), ("+tiles", main, params),
                               ("+skip1e-3", main, p_skip)):
@@ -420,7 +420,7 @@ def run_ours(args, ws, rank, local):
         rows = []
         exact = None
         for thr in (0.0, 1e-5, 1e-4, 3e-4, 1e-3, 3e-3, 1e-2):
-            pp = api.make_params(**{**wl.params, "skip_weight": thr}, **layout)
+            pp = api.make_params(**{**wl.params, "skip_weight": thr}, **layout, appearance=args.appearance)
             for _ in range(args.warmup):
                 api.generate_rays(cams, out=(o, d, tm))
                 api.render_fwd(main, o, d, pp, time=tm, out=(rgb, T, steps))
