@@ -211,9 +211,20 @@ struct Taps {
   float gxs, gys;  // d(texel x, y)/d(u, v): R/2 inside, 0 where clamped
 };
 
+// FAST: q = d * approx(1/l1) (per-step surface directions of appearance 1);
+// else correctly rounded quotients (once per ray)
+template <bool FAST = false>
 __device__ __forceinline__ Taps taps_for(float3 d, int R) {
   float l1 = __fadd_rn(__fadd_rn(fabsf(d.x), fabsf(d.y)), fabsf(d.z));
-  float qx = __fdiv_rn(d.x, l1), qy = __fdiv_rn(d.y, l1);
+  float qx, qy;
+  if (FAST) {
+    const float il = __fdividef(1.f, l1);
+    qx = d.x * il;
+    qy = d.y * il;
+  } else {
+    qx = __fdiv_rn(d.x, l1);
+    qy = __fdiv_rn(d.y, l1);
+  }
   float u, v;
   if (d.z >= 0.f) {
     u = qx;
@@ -249,7 +260,7 @@ __device__ __forceinline__ void tap_weights(const Taps& t, float w[4]) {
 // (gu, gv) . d(u, v)/d(dir) for the octahedral map (Sec. 5.1) of `dir`
 __device__ __forceinline__ float3 oct_vjp(float3 dir, float gu, float gv) {
   const float l1 = fabsf(dir.x) + fabsf(dir.y) + fabsf(dir.z);
-  const float il = 1.f / l1;
+  const float il = __fdividef(1.f, l1);
   const float qx = dir.x * il, qy = dir.y * il;
   const float sx = dir.x >= 0.f ? 1.f : -1.f, sy = dir.y >= 0.f ? 1.f : -1.f, sz = dir.z >= 0.f ? 1.f : -1.f;
   // dq_a/ddir_j = (delta_aj - q_a sgn(dir_j)) / l1
@@ -698,7 +709,7 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
       float tw[4];
       // appearance 1: surface direction, its taps, and the colour gradient terms
       float3 dsurf = make_float3(0.f, 0.f, 0.f);
-      float rlen = 0.f, gt_col = 0.f;
+      float rinv = 0.f, gt_col = 0.f;  // rinv: 1/|x - p| of the surface point (0: none)
       float3 gx_col = make_float3(0.f, 0.f, 0.f);
       Taps tv{0, 0, 0, 0.f, 0.f, 0.f, 0.f};
       float wv[4] = {0.f, 0.f, 0.f, 0.f};
@@ -727,10 +738,11 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
               const float tx = bj >= 0 ? dt : __fsub_rn(t1, th);
               vs = make_float3(__fmaf_rn(tx, d.x, -r.x), __fmaf_rn(tx, d.y, -r.y), __fmaf_rn(tx, d.z, -r.z));
             }
-            rlen = sqrtf(vs.x * vs.x + vs.y * vs.y + vs.z * vs.z);
-            const float il = rlen > 0.f ? 1.f / rlen : rsqrtf(dd);
-            dsurf = rlen > 0.f ? make_float3(vs.x * il, vs.y * il, vs.z * il) : make_float3(d.x * il, d.y * il, d.z * il);
-            tv = taps_for(dsurf, S.R);
+            const float ss = vs.x * vs.x + vs.y * vs.y + vs.z * vs.z;
+            rinv = ss > 0.f ? rsqrtf(ss) : 0.f;  // 1/|x - p|
+            const float il = ss > 0.f ? rinv : rsqrtf(dd);
+            dsurf = ss > 0.f ? make_float3(vs.x * il, vs.y * il, vs.z * il) : make_float3(d.x * il, d.y * il, d.z * il);
+            tv = taps_for<true>(dsurf, S.R);
             tap_weights(tv, wv);
             tbv = (int64_t)cell * S.RR + tv.base;
             const int64_t tbd = tb0;  // view-dependent taps of this cell
@@ -748,9 +760,9 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
                              tw[2] * b2.y + tw[3] * b3.y;
             const float z2 = wv[0] * a0.z + wv[1] * a1.z + wv[2] * a2.z + wv[3] * a3.z + tw[0] * b0.z + tw[1] * b1.z +
                              tw[2] * b2.z + tw[3] * b3.z;
-            c0 = 1.f / (1.f + __expf(-z0));
-            c1 = 1.f / (1.f + __expf(-z1));
-            c2 = 1.f / (1.f + __expf(-z2));
+            c0 = __fdividef(1.f, 1.f + __expf(-z0));
+            c1 = __fdividef(1.f, 1.f + __expf(-z1));
+            c2 = __fdividef(1.f, 1.f + __expf(-z2));
             if (MODE == BWD) {
               // dL/dz = g w c (1 - c); through the bilinear fetch and the octahedral
               // map into the surface direction, then into x and the site
@@ -764,10 +776,10 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
                                          gz1 * ((1.f - tv.fx) * (a2.y - a0.y) + tv.fx * (a3.y - a1.y)) +
                                          gz2 * ((1.f - tv.fx) * (a2.z - a0.z) + tv.fx * (a3.z - a1.z)));
               const float3 gd = oct_vjp(dsurf, gu, gv);
-              if (rlen > 0.f) {
+              if (rinv > 0.f) {
                 const float dg = gd.x * dsurf.x + gd.y * dsurf.y + gd.z * dsurf.z;
-                gx_col = make_float3((gd.x - dsurf.x * dg) / rlen, (gd.y - dsurf.y * dg) / rlen,
-                                     (gd.z - dsurf.z * dg) / rlen);
+                gx_col = make_float3((gd.x - dsurf.x * dg) * rinv, (gd.y - dsurf.y * dg) * rinv,
+                                     (gd.z - dsurf.z * dg) * rinv);
                 gt_col = gx_col.x * d.x + gx_col.y * d.y + gx_col.z * d.z;
               }
             }
