@@ -1114,3 +1114,33 @@ def test_oracle_matches_stored_golden_values():
         tb = np.array([np.inf if t is None else t for t in b["t_exit"]])
         assert np.array_equal(np.isinf(ta), np.isinf(tb)) and np.allclose(ta[np.isfinite(ta)], tb[np.isfinite(tb)],
                                                                              rtol=1e-13, atol=0)
+
+
+def test_joint_translation_of_both_sites_moves_the_crossing():
+    """Plane-crossing derivatives: moving both sites of the crossed face by the
+    same e moves the crossing like moving the ray origin by -e (only the
+    relative geometry matters), so the sum of the two site gradients equals the
+    finite difference of that joint translation (two-cell scene, one ray)."""
+    s1, s2 = np.array([0.0, 0.0, 0.0]), np.array([1.0, 0.2, -0.1])
+    c1, c2 = np.array([1.0, 0.0, 0.0]), np.array([0.0, 0.0, 1.0])
+    tex = np.stack([np.broadcast_to(c1, (4, 4, 3)), np.broadcast_to(c2, (4, 4, 3))])
+    o = np.array([-1.0, 0.05, 0.02])
+    d = np.array([1.0, 0.1, 0.0])
+    d /= np.linalg.norm(d)
+    g = np.array([0.7, -0.3, 0.5])
+    p = O.make_params(t_far=4.0, T_eps=0.0, bg=(0.2, 0.2, 0.2))
+
+    def loss(a, b):
+        sc = O.OracleScene(np.stack([a, b]), [0.9, 2.5], tex, [0, 1, 2], np.array([1, 0], np.int32))
+        return float(g @ O.render(sc, o[None], d[None], params=p)[0][0]), sc
+
+    _, sc = loss(s1, s2)
+    gs, _, _ = O.render_bwd(sc, o[None], d[None], g[None], params=p)
+    n = s2 - s1
+    for e in np.eye(3):
+        h = 1e-6
+        fd = (loss(s1 + h * e, s2 + h * e)[0] - loss(s1 - h * e, s2 - h * e)[0]) / (2 * h)
+        assert abs(fd - (gs[0] + gs[1]) @ e) < 1e-7
+    # and the sum is parallel to n: a joint move within the face plane does not move the crossing
+    tot = gs[0] + gs[1]
+    assert np.linalg.norm(np.cross(tot, n)) <= 1e-12 * max(1.0, np.linalg.norm(tot))
