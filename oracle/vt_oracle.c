@@ -41,7 +41,10 @@
  *   sign(0) = +1 in the lower-hemisphere unfold; texel coordinates clamp to
  *   the edge; exact t ties keep the lower CSR position; termination is tested
  *   after compositing the current cell; the background is added with the final
- *   transmittance; skip rule "w < skip_weight -> no colour, keep T".
+ *   transmittance; skip rule "w < skip_weight -> no colour, keep T"; the
+ *   distortion loss runs over the composited intervals of the walk (after early
+ *   termination) with t the ray parameter; motion blur samples the exposure
+ *   [0, 1) in S jittered strata with linear camera motion.
  *
  * Parity pins for every function live in tests/test_oracle_pins.py. The
  * skip_weight > 0 rule is "parity unpinned" against the paper (the paper
