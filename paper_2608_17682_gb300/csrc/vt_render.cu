@@ -37,7 +37,10 @@ enum Mode { FWD = 0, BWD = 1, TRACE = 2 };
 #define VT_FWD_MINB 4
 #endif
 #ifndef VT_BWD_MINB
-#define VT_BWD_MINB 3
+#define VT_BWD_MINB 4  // plain backward (appearance 0, no distortion): 349.5 vs 345.9 Mrays/s at 3
+#endif
+#ifndef VT_BWD_MINB_EXT
+#define VT_BWD_MINB_EXT 3  // backward with the paper's appearance model or the distortion loss
 #endif
 // 1: issue a cell's texel loads before its exit search (latency overlapped,
 // more live registers); 0: after it
@@ -518,13 +521,14 @@ __device__ __forceinline__ void ff_fma_acc(float& hi, float& lo, float w, float 
   hi = s;
 }
 
-template <int MODE>
+template <int MODE, int APP, int DIST>
 struct WalkBounds {
-  static constexpr int minb = MODE == FWD ? VT_FWD_MINB : (MODE == BWD ? VT_BWD_MINB : 2);
+  static constexpr int minb =
+      MODE == FWD ? VT_FWD_MINB : (MODE == BWD ? ((APP || DIST) ? VT_BWD_MINB_EXT : VT_BWD_MINB) : 2);
 };
 
 template <int MODE, int DT, int APP, int DIST, int HALF>
-__global__ void __launch_bounds__(256, WalkBounds<MODE>::minb)
+__global__ void __launch_bounds__(256, WalkBounds<MODE, APP, DIST>::minb)
     k_walk(Scene S, RP P, const float* __restrict__ O, const float* __restrict__ D,
            const int32_t* __restrict__ anchor_cell, float* __restrict__ rgb_out, float* __restrict__ T_out,
            int32_t* __restrict__ steps_out, Grad G, Trace TR) {
