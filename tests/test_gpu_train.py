@@ -85,18 +85,6 @@ def test_adam_kernel():
     assert np.abs(tp.cpu().numpy() - rp).max() <= 2e-6
 
 
-def test_learning_rate_schedules():
-    cfg = T.TrainConfig(iters=20_000)
-    a = T.learning_rates(cfg, 0)
-    assert abs(a["sites"] - 2e-4) < 1e-12 and abs(a["tex"] - 2e-2) < 1e-12
-    assert a["tex_vd"] == 0.0  # quadratic ramp starts at zero
-    assert abs(T.learning_rates(cfg, 999)["rho"] - 0.05) < 1e-12  # linear warm-up over 2,000 iterations
-    assert abs(T.learning_rates(cfg, 2000)["rho"] - 0.1) < 1e-12
-    assert abs(T.learning_rates(cfg, 4000)["tex_vd"] - T.learning_rates(cfg, 4000)["tex"]) < 1e-15
-    assert T.learning_rates(cfg, 18_000)["sites"] == 0.0  # sites fixed for the last 2,000 iterations
-    assert abs(T.learning_rates(cfg, 19_999)["tex"] - 5e-4) < 1e-6
-
-
 def test_training_reduces_loss_with_delaunay_refresh():
     init, cams, images, rp, gt = T.synthetic_problem(n_sites=4000, n_cams=6, w=64, h=48, tex_res=4, seed=3)
     cfg = T.TrainConfig(iters=120, rays_per_iter=8192, refresh_every=40, vd_ramp_frac=0.0, seed=1)

@@ -108,3 +108,19 @@ def test_camera_set_of_mixed_workload():
     assert sum(c.n_rays for c in cams) == 29_818_880
     cams = W.workload_cameras("prec3m")
     assert sum(c.n_rays for c in cams) == 4 * 1280 * 832
+
+
+def test_learning_rate_schedules():
+    """The appendix's schedules: cosine decays, linear density warm-up over the
+    first 10%, sites fixed for the last 10%, quadratic view-dependent ramp."""
+    from paper_2608_17682_gb300 import train as T
+
+    cfg = T.TrainConfig(iters=20_000)
+    a = T.learning_rates(cfg, 0)
+    assert abs(a["sites"] - 2e-4) < 1e-12 and abs(a["tex"] - 2e-2) < 1e-12
+    assert a["tex_vd"] == 0.0  # quadratic ramp starts at zero
+    assert abs(T.learning_rates(cfg, 999)["rho"] - 0.05) < 1e-12  # linear warm-up over 2,000 iterations
+    assert abs(T.learning_rates(cfg, 2000)["rho"] - 0.1) < 1e-12
+    assert abs(T.learning_rates(cfg, 4000)["tex_vd"] - T.learning_rates(cfg, 4000)["tex"]) < 1e-15
+    assert T.learning_rates(cfg, 18_000)["sites"] == 0.0  # sites fixed for the last 2,000 iterations
+    assert abs(T.learning_rates(cfg, 19_999)["tex"] - 5e-4) < 1e-6
