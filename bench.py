@@ -20,6 +20,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -133,11 +134,21 @@ def measured_peaks():
         return {"hbm_gbs": HBM_FALLBACK_GBS}, "fallback"
 
 
+def _code_only(text):
+    """Source text without comments and blank space, so that a comment edit
+    does not count as a kernel change."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash():
+    """Hash of the CUDA sources' code (comments and spacing ignored)."""
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2608_17682_gb300", "csrc"))):
-        with open(os.path.join(ROOT, "paper_2608_17682_gb300", "csrc", f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+    d = os.path.join(ROOT, "paper_2608_17682_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), encoding="utf-8") as fh:
+            h.update(f.encode() + _code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -1,9 +1,10 @@
 // vt_render.cu -- start-cell search, Voronoi walk, compositing, adjoint.
 //
 // One thread per ray; a warp covers a 4 x 8 tile of an image (Sec. 5.6
-// "warp-coherent tiling") so neighbouring threads walk similar cells and
-// share cache lines. Forward, backward and trace are one templated kernel
-// whose walk is the same inline code, so their decisions are identical.
+// "warp-coherent tiling", 8 pixels wide, 4 tall) and a 256-thread block a
+// 16 x 16-pixel patch of such tiles, so neighbouring threads walk similar
+// cells and share cache lines. Forward, backward and trace are one templated
+// kernel whose walk is the same inline code, so their decisions are identical.
 //
 // Exit test (Sec. 3.1): from cell i, entered at ray parameter t, the exit is
 // the nearest forward crossing over the Delaunay neighbours j of
@@ -13,12 +14,18 @@
 // the cell size instead of the distance from the origin. Candidates are
 // compared by cross-multiplication (no division in the loop). A plane with
 // |n.d| <= 1e-6 |n||d| (grazing; FP32 cannot fix the sign of n.d) is
-// re-evaluated in FP64 from the FP32 site positions.
+// re-evaluated in FP64 from the FP32 site positions, in a second pass over the
+// cell that runs only when the loop met such a plane.
 //
 // Compositing (Sec. 3.2): alpha = 1 - exp(-sigma delta), w = T alpha,
 // C += w c, T *= (1 - alpha); stop once T < T_eps after compositing a cell.
 // Colour (Sec. 5.1): bilinear fetch of the cell's octahedral texture at the
-// ray direction; the four taps are fixed per ray.
+// ray direction; the four taps are fixed per ray. Appearance 1 is the paper's
+// model (Sec. 5.1-5.2): a surface texture at the entry point's direction from
+// the site plus a view-dependent texture at -d, summed as logits, sigmoid.
+// The distortion loss (Eq. 2) can ride in the same walk (template DIST).
+// Backward gradients go to Morton-ordered scratch through warp-aggregated
+// vector atomics and are permuted to the caller's order by k_grad_out.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -31,8 +38,8 @@ namespace {
 enum Mode { FWD = 0, BWD = 1, TRACE = 2 };
 
 // minimum resident 256-thread blocks per SM requested for the walk kernels
-// (forward: more warps hide the walk's dependent loads; backward: more
-// registers for the adjoint state)
+// (more warps hide the walk's dependent loads; the appearance-1 and
+// distortion backwards keep more registers for their adjoint state)
 #ifndef VT_FWD_MINB
 #define VT_FWD_MINB 4
 #endif
