@@ -124,3 +124,30 @@ def test_learning_rate_schedules():
     assert abs(T.learning_rates(cfg, 4000)["tex_vd"] - T.learning_rates(cfg, 4000)["tex"]) < 1e-15
     assert T.learning_rates(cfg, 18_000)["sites"] == 0.0  # sites fixed for the last 2,000 iterations
     assert abs(T.learning_rates(cfg, 19_999)["tex"] - 5e-4) < 1e-6
+
+
+def test_traffic_record_survives_comment_edits(tmp_path):
+    """bench.py keys recorded DRAM traffic to the kernel sources' code: a
+    comment edit keeps the record, a code edit drops it."""
+    import shutil
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    src = os.path.join(bench.ROOT, "paper_2608_17682_gb300", "csrc")
+    dst = tmp_path / "paper_2608_17682_gb300" / "csrc"
+    shutil.copytree(src, dst)
+    (tmp_path / "profiles").mkdir()
+    old_root = bench.ROOT
+    try:
+        bench.ROOT = str(tmp_path)
+        h = bench.kernel_source_hash()
+        (tmp_path / "profiles" / "x.md").write_text(f"TRAFFIC k_walk<BWD> prec3m 123 {h}\n")
+        assert bench.recorded_traffic("k_walk<BWD>", "prec3m") == 123
+        f = dst / "vt_render.cu"
+        f.write_text(f.read_text() + "\n// a comment\n/* another */\n")
+        assert bench.kernel_source_hash() == h
+        f.write_text(f.read_text() + "\nstatic int extra_symbol_for_test;\n")
+        assert bench.kernel_source_hash() != h
+        assert bench.recorded_traffic("k_walk<BWD>", "prec3m") is None
+    finally:
+        bench.ROOT = old_root
