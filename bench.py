@@ -500,7 +500,8 @@ def run_ours(args, ws, rank, local):
     alg = sum_steps * (b_bwd_step if dom == "bwd" else b_fwd_step) + n_rays * (io_bwd if dom == "bwd" else io_fwd)
     achieved = alg / (ms_dom * 1e-3) / 1e9
     peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
-    kname = "k_walk<BWD>" if dom == "bwd" else "k_walk<FWD>"
+    # the walk instantiation: mode, texel storage, appearance model
+    kname = f"k_walk<{dom.upper()},{args.tex}" + (",appearance1>" if args.appearance else ">")
     roof = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": recorded_traffic(kname, args.workload),
             "algorithmic_bytes_per_launch": int(alg), "peak_source": f"{peak_kind} hbm_gbs",

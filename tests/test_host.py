@@ -141,13 +141,14 @@ def test_traffic_record_survives_comment_edits(tmp_path):
     try:
         bench.ROOT = str(tmp_path)
         h = bench.kernel_source_hash()
-        (tmp_path / "profiles" / "x.md").write_text(f"TRAFFIC k_walk<BWD> prec3m 123 {h}\n")
-        assert bench.recorded_traffic("k_walk<BWD>", "prec3m") == 123
+        (tmp_path / "profiles" / "x.md").write_text(f"TRAFFIC k_walk<BWD,f16> prec3m 123 {h}\n")
+        assert bench.recorded_traffic("k_walk<BWD,f16>", "prec3m") == 123
+        assert bench.recorded_traffic("k_walk<BWD,f32>", "prec3m") is None
         f = dst / "vt_render.cu"
         f.write_text(f.read_text() + "\n// a comment\n/* another */\n")
         assert bench.kernel_source_hash() == h
         f.write_text(f.read_text() + "\nstatic int extra_symbol_for_test;\n")
         assert bench.kernel_source_hash() != h
-        assert bench.recorded_traffic("k_walk<BWD>", "prec3m") is None
+        assert bench.recorded_traffic("k_walk<BWD,f16>", "prec3m") is None
     finally:
         bench.ROOT = old_root
