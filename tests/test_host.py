@@ -3,6 +3,7 @@ symbol include/vt.h declares, host argument validation, workload inputs."""
 import os
 import re
 import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -152,3 +153,20 @@ def test_traffic_record_survives_comment_edits(tmp_path):
         assert bench.recorded_traffic("k_walk<BWD,f16>", "prec3m") is None
     finally:
         bench.ROOT = old_root
+
+
+def test_reference_arm_json_line():
+    """bench.py --impl reference times the oracle on the host and prints one
+    JSON line with the contract's keys (runs without a GPU)."""
+    import json
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "tiny", "--steps", "1",
+                          "--warmup", "1"], cwd=root, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    j = json.loads(lines[0])
+    assert j["impl"] == "reference" and j["unit"] == "Mrays/s" and j["value"] > 0 and j["higher_is_better"]
+    assert j["cpu_baseline"]["kind"] == "oracle" and j["cpu_baseline"]["value"] == j["value"]
+    assert j["e2e"]["h2d_bytes_per_step"] == 0 and j["e2e"]["d2h_bytes_per_step"] == 0
+    assert j["steps"] == 1 and j["warmup"] == 1 and j["n_gpus"] == 1
