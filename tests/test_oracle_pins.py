@@ -1144,3 +1144,60 @@ def test_joint_translation_of_both_sites_moves_the_crossing():
     # and the sum is parallel to n: a joint move within the face plane does not move the crossing
     tot = gs[0] + gs[1]
     assert np.linalg.norm(np.cross(tot, n)) <= 1e-12 * max(1.0, np.linalg.norm(tot))
+
+
+def test_fd_distortion_rays_starting_inside_with_termination():
+    """Distortion loss for origins inside the crop (first interval starts at
+    t_near = 0, not at a crossing) and with early termination at T < 1e-2:
+    FD of sum gd L_dist for densities and sites against the adjoint."""
+    sc, _, _, _, params = crop_setup()
+    rng = np.random.default_rng(31)
+    lo, hi = np.array(params["clip_lo"]), np.array(params["clip_hi"])
+    c = 0.5 * (lo + hi)
+    n = 300
+    o = c + rng.uniform(-0.05, 0.05, size=(n, 3))
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    p = O.make_params(**dict(params, T_eps=1e-2))
+    osc = O.OracleScene.from_workload_scene(sc)
+    _, T, _, flags = O.render(osc, o, d, params=p, n_threads=1)
+    keep = (flags & O.BAND_FLAGS) == 0  # rays near a degenerate configuration are left out
+    o, d, T = o[keep], d[keep], T[keep]
+    n = len(o)
+    assert (T < 1e-2).sum() > 20  # some rays terminate early
+    gd = rng.uniform(0.5, 1.5, size=n)
+    gs, gsig, _ = O.render_bwd(osc, o, d, np.zeros((n, 3)), params=p, grad_dist=gd)
+    base_cells = O.trace(osc, o, d, params=p, n_threads=1)[0]
+
+    def F(sites=osc.sites, sigma=osc.sigma):
+        sc2 = O.OracleScene(sites, sigma, osc.tex, sc.offsets, sc.indices)
+        return float(gd @ O.distortion(sc2, o, d, params=p, n_threads=1)), sc2
+
+    for i in rng.choice(np.nonzero(np.abs(gsig) > 1e-9)[0], size=12, replace=False):
+        h = 1e-6 * max(1.0, osc.sigma[i])
+        v = []
+        for sgn in (1, -1):
+            sg = osc.sigma.copy()
+            sg[i] += sgn * h
+            v.append(F(sigma=sg)[0])
+        fd = (v[0] - v[1]) / (2 * h)
+        assert abs(fd - gsig[i]) <= 1e-4 * max(abs(gsig[i]), 1e-3 * np.abs(gsig).max()), (i, fd, gsig[i])
+    checked = 0
+    for q in np.argwhere(np.abs(gs) > 1e-9)[rng.permutation(int((np.abs(gs) > 1e-9).sum()))]:
+        i, k = int(q[0]), int(q[1])
+        v = []
+        for sgn in (1, -1):
+            ss = osc.sites.copy()
+            ss[i, k] += sgn * 1e-7
+            val, sc2 = F(sites=ss)
+            if not np.array_equal(O.trace(sc2, o, d, params=p, n_threads=1)[0], base_cells):
+                break
+            v.append(val)
+        if len(v) < 2:
+            continue
+        fd = (v[0] - v[1]) / 2e-7
+        assert abs(fd - gs[i, k]) <= 1e-4 * max(abs(gs[i, k]), 1e-3 * np.abs(gs).max()), (i, k, fd, gs[i, k])
+        checked += 1
+        if checked >= 12:
+            break
+    assert checked >= 10
