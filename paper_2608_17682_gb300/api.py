@@ -30,6 +30,26 @@ def _dev_f32(x, device):
     return torch.as_tensor(x, dtype=torch.float32, device=device).contiguous()
 
 
+def _arr(t, name, shape, dtype=torch.float32, optional=False):
+    """Checks a tensor the library reads or writes through a raw pointer: a
+    C-contiguous CUDA tensor of `dtype` and `shape`. A wrong one would make the
+    kernels read or write outside it, so it is rejected before any call."""
+    if t is None:
+        if optional:
+            return
+        raise ValueError(f"{name} is required")
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name} must be a torch tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+
+
 class Scene:
     """A Voronoi scene resident on the GPU (library-owned, Morton-ordered)."""
 
@@ -67,6 +87,12 @@ class Scene:
 
     def update(self, sites=None, sigma=None, tex=None, tex_vd=None):
         keep = [None if x is None else _dev_f32(x, self.device) for x in (sites, sigma, tex, tex_vd)]
+        n, R = self.n, self.R
+        for x, name, shape in zip(keep, ("sites", "sigma", "tex", "tex_vd"),
+                                  ((n, 3), (n,), (n, R, R, 3), (n, R, R, 3))):
+            _arr(x, name, shape, optional=True)
+        if keep[3] is not None and not self.has_tex_vd:
+            raise ValueError("tex_vd given for a scene built without one")
         _vt.vt_scene_update(self.handle, *[_ptr(x) for x in keep], _stream())
 
     def get_error(self):
@@ -130,6 +156,9 @@ def generate_rays(cameras, device="cuda", out=None):
         t = torch.empty(n, device=device)
     else:
         o, d, t = out
+        _arr(o, "o", (n, 3))
+        _arr(d, "d", (n, 3))
+        _arr(t, "time", (n,))
     _vt.vt_generate_rays(cs, o.data_ptr(), d.data_ptr(), t.data_ptr(), _stream())
     return o, d, t
 
@@ -140,12 +169,20 @@ def render_fwd(scene: Scene, o, d, params, time=None, out=None, want_steps=True,
     exact backward. If `dist` is a [n,3] tensor it receives the distortion
     loss per ray (column 0, Eq. 2) and the two totals the backward needs."""
     n = o.shape[0]
+    _arr(o, "o", (n, 3))
+    _arr(d, "d", (n, 3))
+    _arr(time, "time", (n,), optional=True)
+    _arr(residual, "residual", (n, 3), optional=True)
+    _arr(dist, "dist", (n, 3), optional=True)
     if out is None:
         rgb = torch.empty(n, 3, device=o.device)
         T = torch.empty(n, device=o.device)
         steps = torch.empty(n, dtype=torch.int32, device=o.device) if want_steps else None
     else:
         rgb, T, steps = out
+    _arr(rgb, "rgb", (n, 3))
+    _arr(T, "T", (n,), optional=True)
+    _arr(steps, "steps", (n,), dtype=torch.int32, optional=True)
     _vt.vt_render_fwd(scene.handle, n, o.data_ptr(), d.data_ptr(), _ptr(time), params, rgb.data_ptr(), _ptr(T),
                       _ptr(steps), _ptr(residual), _ptr(dist), _stream())
     return rgb, T, steps
@@ -158,22 +195,33 @@ def render_bwd(scene: Scene, o, d, params, rgb, grad_rgb, time=None, out=None, n
     With `grad_dist` ([n], dL/dL_dist per ray) the distortion loss is included;
     `dist` is then the forward's `dist` output."""
     dev = o.device
+    n, N, R = o.shape[0], scene.n, scene.R
     if out is None:
-        gs = torch.empty(scene.n, 3, device=dev) if need[0] else None
-        gsig = torch.empty(scene.n, device=dev) if need[1] else None
-        gt = torch.empty(scene.n, scene.R, scene.R, 3, device=dev) if need[2] else None
+        gs = torch.empty(N, 3, device=dev) if need[0] else None
+        gsig = torch.empty(N, device=dev) if need[1] else None
+        gt = torch.empty(N, R, R, 3, device=dev) if need[2] else None
     else:
         gs, gsig, gt = out
+    grad_rgb = grad_rgb.contiguous()
     if grad_dist is not None:
         grad_dist = grad_dist.contiguous()
-    _vt.vt_render_bwd(scene.handle, o.shape[0], o.data_ptr(), d.data_ptr(), _ptr(time), params, rgb.data_ptr(),
-                      _ptr(residual), _ptr(dist), grad_rgb.contiguous().data_ptr(), _ptr(grad_dist), _ptr(gs),
+    for t, name, shape, opt in ((o, "o", (n, 3), False), (d, "d", (n, 3), False), (rgb, "rgb", (n, 3), False),
+                                (grad_rgb, "grad_rgb", (n, 3), False), (time, "time", (n,), True),
+                                (residual, "residual", (n, 3), True), (dist, "dist", (n, 3), True),
+                                (grad_dist, "grad_dist", (n,), True), (gs, "grad_sites", (N, 3), True),
+                                (gsig, "grad_sigma", (N,), True), (gt, "grad_tex", (N, R, R, 3), True),
+                                (tex_vd_out, "tex_vd_out", (N, R, R, 3), True)):
+        _arr(t, name, shape, optional=opt)
+    _vt.vt_render_bwd(scene.handle, n, o.data_ptr(), d.data_ptr(), _ptr(time), params, rgb.data_ptr(),
+                      _ptr(residual), _ptr(dist), grad_rgb.data_ptr(), _ptr(grad_dist), _ptr(gs),
                       _ptr(gsig), _ptr(gt), _ptr(tex_vd_out), _stream())
     return gs, gsig, gt
 
 
 def trace_cells(scene: Scene, o, d, params, max_cells=512):
     n = o.shape[0]
+    _arr(o, "o", (n, 3))
+    _arr(d, "d", (n, 3))
     cells = torch.full((n, max_cells), -1, dtype=torch.int32, device=o.device)
     t_exit = torch.full((n, max_cells), float("nan"), device=o.device)
     n_cells = torch.empty(n, dtype=torch.int32, device=o.device)
@@ -184,14 +232,20 @@ def trace_cells(scene: Scene, o, d, params, max_cells=512):
 
 def l2_loss(rgb, target):
     n = rgb.shape[0]
-    grad = torch.empty_like(rgb)
+    target = target.contiguous()
+    _arr(rgb, "rgb", (n, 3))
+    _arr(target, "target", (n, 3))
+    grad = torch.empty(n, 3, device=rgb.device)
     loss = torch.empty(1, device=rgb.device)
-    _vt.vt_l2_loss(n, rgb.data_ptr(), target.contiguous().data_ptr(), grad.data_ptr(), loss.data_ptr(), _stream())
+    _vt.vt_l2_loss(n, rgb.data_ptr(), target.data_ptr(), grad.data_ptr(), loss.data_ptr(), _stream())
     return loss, grad
 
 
 def average_samples(rgb_rays, spp):
+    if spp < 1 or rgb_rays.shape[0] % spp:
+        raise ValueError("the ray count must be a multiple of spp >= 1")
     n_px = rgb_rays.shape[0] // spp
+    _arr(rgb_rays, "rgb_rays", (n_px * spp, 3))
     out = torch.empty(n_px, 3, device=rgb_rays.device)
     _vt.vt_average_samples(n_px, spp, rgb_rays.data_ptr(), out.data_ptr(), _stream())
     return out
@@ -200,6 +254,7 @@ def average_samples(rgb_rays, spp):
 def sigma_from_rho(rho):
     """sigma = exp(rho) (Sec. 5.4) on the GPU."""
     rho = rho.contiguous()
+    _arr(rho, "rho", tuple(rho.shape))
     out = torch.empty_like(rho)
     _vt.vt_sigma_from_rho(rho.numel(), rho.data_ptr(), out.data_ptr(), _stream())
     return out
@@ -207,9 +262,11 @@ def sigma_from_rho(rho):
 
 def sigma_from_rho_bwd(sigma, grad_sigma):
     """dL/drho = dL/dsigma * sigma (Eq. 4) on the GPU."""
+    sigma, grad_sigma = sigma.contiguous(), grad_sigma.contiguous()
+    _arr(sigma, "sigma", tuple(sigma.shape))
+    _arr(grad_sigma, "grad_sigma", tuple(sigma.shape))
     out = torch.empty_like(sigma)
-    _vt.vt_sigma_from_rho_bwd(sigma.numel(), sigma.contiguous().data_ptr(), grad_sigma.contiguous().data_ptr(),
-                              out.data_ptr(), _stream())
+    _vt.vt_sigma_from_rho_bwd(sigma.numel(), sigma.data_ptr(), grad_sigma.data_ptr(), out.data_ptr(), _stream())
     return out
 
 
@@ -229,8 +286,10 @@ class SigmaFromRho(torch.autograd.Function):
 
 
 def average_samples_bwd(grad_px, spp):
+    grad_px = grad_px.contiguous()
+    _arr(grad_px, "grad_px", (grad_px.shape[0], 3))
     out = torch.empty(grad_px.shape[0] * spp, 3, device=grad_px.device)
-    _vt.vt_average_samples_bwd(grad_px.shape[0], spp, grad_px.contiguous().data_ptr(), out.data_ptr(), _stream())
+    _vt.vt_average_samples_bwd(grad_px.shape[0], spp, grad_px.data_ptr(), out.data_ptr(), _stream())
     return out
 
 

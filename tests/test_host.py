@@ -170,3 +170,41 @@ def test_reference_arm_json_line():
     assert j["cpu_baseline"]["kind"] == "oracle" and j["cpu_baseline"]["value"] == j["value"]
     assert j["e2e"]["h2d_bytes_per_step"] == 0 and j["e2e"]["d2h_bytes_per_step"] == 0
     assert j["steps"] == 1 and j["warmup"] == 1 and j["n_gpus"] == 1
+
+
+def test_api_rejects_tensors_the_kernels_cannot_take():
+    """Tensors reach the kernels as raw pointers, so api.py checks device,
+    dtype, shape and contiguity first and raises before any library call."""
+    import types
+    import torch
+    from paper_2608_17682_gb300 import api
+    from paper_2608_17682_gb300 import workloads as W
+    scene = types.SimpleNamespace(handle=0, n=5, R=4, has_tex_vd=False, device=torch.device("cpu"))
+    P = api.make_params()
+    cpu = torch.zeros(4, 3)
+    for call in (lambda: api.render_fwd(scene, cpu, cpu, P),
+                 lambda: api.render_bwd(scene, cpu, cpu, P, cpu, cpu),
+                 lambda: api.trace_cells(scene, cpu, cpu, P),
+                 lambda: api.l2_loss(cpu, cpu),
+                 lambda: api.average_samples(cpu, 2),
+                 lambda: api.average_samples_bwd(cpu, 2),
+                 lambda: api.sigma_from_rho(torch.zeros(5)),
+                 lambda: api.sigma_from_rho_bwd(torch.zeros(5), torch.zeros(5)),
+                 lambda: api.generate_rays([W.look_at_camera(0, 2, 2, (0.0, -2.0, 0.0), (0.0, 0.0, 0.0))],
+                                           out=(cpu, cpu, torch.zeros(4)))):
+        with pytest.raises(ValueError):
+            call()
+    with pytest.raises(ValueError):  # not a multiple of the sample count
+        api.average_samples(torch.zeros(10, 3), 4)
+    # the checker itself: dtype, shape and contiguity come before the device
+    with pytest.raises(ValueError, match="float32"):
+        api._arr(torch.zeros(4, 3, dtype=torch.float64), "x", (4, 3))
+    with pytest.raises(ValueError, match="shape"):
+        api._arr(torch.zeros(4, 4), "x", (4, 3))
+    with pytest.raises(ValueError, match="contiguous"):
+        api._arr(torch.zeros(3, 4).t(), "x", (4, 3))
+    with pytest.raises(ValueError, match="CUDA"):
+        api._arr(torch.zeros(4, 3), "x", (4, 3))
+    with pytest.raises(ValueError, match="required"):
+        api._arr(None, "x", (4, 3))
+    api._arr(None, "x", (4, 3), optional=True)
