@@ -12,7 +12,7 @@
  * plain definitions of the paper:
  *   - Voronoi cell V_i = points nearest site p_i (Sec. 3.1).
  *   - Start cell = nearest site of the ray origin, by brute force over all
- *     sites (Sec. 3.1, "single nearest-neighbor query"); ties -> lowest id.
+ *     sites (Sec. 3.1: the walk starts from one nearest-site lookup); ties -> lowest id.
  *   - Exit from cell i = nearest forward crossing of the bisector planes with
  *     the Delaunay neighbours j (Sec. 3.1 and its walk figure):
  *       t_j = n.((s_i+s_j)/2 - o) / (n.d),  n = s_j - s_i, only n.d > 0.
@@ -21,7 +21,7 @@
  *       C = sum_k T_k alpha_k c_k + T_final * bg,
  *     stopping after the cell at which T < T_eps (early termination, Sec. 3.2).
  *   - Colour = bilinear fetch of the cell's R x R octahedral texture at the
- *     ray direction (Sec. 5.1 octahedral map, read "at the ray direction");
+ *     ray direction (Sec. 5.1 octahedral map, evaluated at the ray direction);
  *     or, in appearance mode 1, the paper's model (Sec. 5.1-5.2):
  *       c = sigmoid(T_vi(oct((x - p_i)/|x - p_i|)) + T_vd(oct(omega))),
  *     x = the point where the ray enters the cell (for the cell holding the

@@ -1,7 +1,7 @@
 // vt_render.cu -- start-cell search, Voronoi walk, compositing, adjoint.
 //
-// One thread per ray; a warp covers a 4 x 8 tile of an image (Sec. 5.6
-// "warp-coherent tiling", 8 pixels wide, 4 tall) and a 256-thread block a
+// One thread per ray; a warp covers a 4 x 8 tile of an image (the warp-coherent
+// tiling of Sec. 5.6, 8 pixels wide, 4 tall) and a 256-thread block a
 // 16 x 16-pixel patch of such tiles, so neighbouring threads walk similar
 // cells and share cache lines. Forward, backward and trace are one templated
 // kernel whose walk is the same inline code, so their decisions are identical.
