@@ -95,7 +95,7 @@ typedef struct {
 
 /* ------------------------------------------------------------------ */
 /* Octahedral map, Sec. 5.1: l1-normalise, upper hemisphere maps to the
- * central diamond, lower hemisphere is unfolded to the corners.        */
+ * central diamond, points with z < 0 fold out into the four corners.   */
 int vto_oct(const double d[3], double uv[2]) {
   double l1 = fabs(d[0]) + fabs(d[1]) + fabs(d[2]);
   if (!(l1 > 0.0) || !isfinite(l1)) return VTO_ERR_ARG;
