@@ -41,15 +41,14 @@
  *   sign(0) = +1 in the lower-hemisphere unfold; texel coordinates clamp to
  *   the edge; exact t ties keep the lower CSR position; termination is tested
  *   after compositing the current cell; the background is added with the final
- *   transmittance; skip rule "w < skip_weight -> no colour, keep T"; the
+ *   transmittance; the skip test is strict (w < skip_weight skips); the
  *   distortion loss runs over the composited intervals of the walk (after early
  *   termination) with t the ray parameter; motion blur samples the exposure
  *   [0, 1) in S jittered strata with linear camera motion.
  *
- * Parity pins for every function live in tests/test_oracle_pins.py. The
- * skip_weight > 0 rule is "parity unpinned" against the paper (the paper
- * prints only PSNR deltas for it); it is pinned only against its own
- * definition.
+ * Parity pins for every function live in tests/test_oracle_pins.py; the
+ * skip_weight > 0 rule (Sec. 5.6: below the threshold a cell attenuates T but
+ * adds no colour) is pinned by a two-cell closed form of colour and adjoint.
  */
 #include <math.h>
 #include <pthread.h>

@@ -259,6 +259,60 @@ def test_closed_form_two_cells():
     assert steps[0] == 2
 
 
+def test_skip_rule_two_cells_closed_form_and_adjoint():
+    """Cell skipping (Sec. 5.6, read as: a cell whose weight w = T alpha is
+    below the threshold adds no colour but still attenuates T). Two cells, the
+    first too thin to pass the threshold: closed forms for C, for dC/dsigma of
+    both cells and for the texel gradients, and the threshold-free limit."""
+    s1, s2 = np.array([0.0, 0.0, 0.0]), np.array([1.0, 0.2, -0.1])
+    c1, c2 = np.array([1.0, 0.0, 0.0]), np.array([0.0, 0.0, 1.0])
+    bg = np.array([0.3, 0.6, 0.9])
+    tex = np.stack([np.broadcast_to(c1, (4, 4, 3)), np.broadcast_to(c2, (4, 4, 3))])
+    sig1, sig2 = 0.02, 2.5
+    sc = O.OracleScene(np.stack([s1, s2]), [sig1, sig2], tex, [0, 1, 2], np.array([1, 0], np.int32))
+    o = np.array([-1.0, 0.05, 0.02])
+    d = np.array([1.0, 0.1, 0.0])
+    d /= np.linalg.norm(d)
+    t_far = 4.0
+    tstar = np.dot(s2 - s1, 0.5 * (s1 + s2) - o) / np.dot(s2 - s1, d)
+    d1, d2 = tstar, t_far - tstar
+    e1, e2 = np.exp(-sig1 * d1), np.exp(-sig2 * d2)
+    w1, w2 = 1 - e1, e1 * (1 - e2)
+    T = e1 * e2
+    skip = 0.1
+    assert w1 < skip < w2
+    kw = dict(t_far=t_far, T_eps=0.0, bg=tuple(bg))
+    rgb, Tout, steps, flags = O.render(sc, o[None], d[None], skip_weight=skip, **kw)
+    assert flags[0] == 0 and steps[0] == 2
+    assert np.allclose(rgb[0], w2 * c2 + T * bg, atol=1e-14)
+    assert abs(Tout[0] - T) < 1e-15
+    g = np.array([0.7, -1.3, 0.4])
+    gs, gsig, gt = O.render_bwd(sc, o[None], d[None], g[None], skip_weight=skip, **kw)
+    # sigma_1 only attenuates what lies behind it; sigma_2 trades background for c2
+    assert abs(gsig[0] - g @ (-d1 * (w2 * c2 + T * bg))) < 1e-13
+    assert abs(gsig[1] - g @ (e1 * d2 * e2 * (c2 - bg))) < 1e-13
+    assert np.all(gt[0] == 0.0)
+    assert np.allclose(gt[1].reshape(-1, 3).sum(0), w2 * g, atol=1e-14)
+    # a threshold below every weight changes nothing
+    ref = O.render(sc, o[None], d[None], skip_weight=0.0, **kw)
+    low = O.render(sc, o[None], d[None], skip_weight=0.5 * w1, **kw)
+    assert np.array_equal(ref[0], low[0]) and np.array_equal(ref[1], low[1])
+    assert np.allclose(ref[0][0], w1 * c1 + w2 * c2 + T * bg, atol=1e-14)
+    # the adjoint agrees with central differences away from the threshold
+    h = 1e-6
+    for i, sg in enumerate((sig1, sig2)):
+        sp, sm = [sig1, sig2], [sig1, sig2]
+        sp[i], sm[i] = sg + h, sg - h
+        fp = O.render(O.OracleScene(np.stack([s1, s2]), sp, tex, [0, 1, 2], np.array([1, 0], np.int32)),
+                      o[None], d[None], skip_weight=skip, **kw)[0][0]
+        fm = O.render(O.OracleScene(np.stack([s1, s2]), sm, tex, [0, 1, 2], np.array([1, 0], np.int32)),
+                      o[None], d[None], skip_weight=skip, **kw)[0][0]
+        assert abs(g @ (fp - fm) / (2 * h) - gsig[i]) < 1e-8
+    # a weight within 1e-4 relative of the threshold is flagged as ambiguous
+    _, _, _, fl = O.render(sc, o[None], d[None], skip_weight=w1 * (1 + 5e-5), **kw)
+    assert fl[0] != 0
+
+
 def test_constant_texture_any_direction():
     c = np.array([0.25, 0.5, 0.75])
     sc = _one_site_scene([0, 0, 0], 3.0, c, R=8)
