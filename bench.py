@@ -286,12 +286,14 @@ def run_ours(args, ws, rank, local):
             en.append(b)
             marks.append(m)
         barrier()
-        total = sum(x.elapsed_time(y) for x, y in zip(st, en))
+        per_step = [x.elapsed_time(y) for x, y in zip(st, en)]
+        total = sum(per_step)
         fwd = sum(m[0].elapsed_time(m[1]) for m in marks) / K
         bwd = 0.0 if fwd_only else sum(m[2].elapsed_time(m[3]) for m in marks) / K
         if walks is not None:
             walks["fwd"] = sum(m[4].elapsed_time(m[5]) for m in marks) / K
             walks["bwd"] = 0.0 if fwd_only else sum(m[6].elapsed_time(m[7]) for m in marks) / K
+            walks["step_median"] = statistics.median(per_step)
         return total / K, fwd, bwd
 
     main = scenes[args.tex]
@@ -511,7 +513,8 @@ def run_ours(args, ws, rank, local):
         "metric": (METRIC if args.tex == "f16" else METRIC.replace("FP16", args.tex.upper()))
         + (", paper appearance model" if args.appearance else ""),
         "value": round(value * 1.0, 3), "unit": "Mrays/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "ms_per_step_median": round(walks["step_median"], 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {N} sites, {R}x{R} {args.tex} textures"
                                f"{' (two maps, sigmoid)' if args.appearance else ''}, "
