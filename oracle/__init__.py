@@ -57,7 +57,9 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
+        # VT_ORACLE_LIB points the wrapper at another build of this source:
+        # the mutation tests load deliberately broken copies through it
+        _lib = C.CDLL(os.environ.get("VT_ORACLE_LIB") or build())
         L = _lib
         L.vto_oct.argtypes = [C.c_void_p, C.c_void_p]
         L.vto_bilinear_taps.argtypes = [C.c_int32, C.c_double, C.c_double, C.c_void_p, C.c_void_p]

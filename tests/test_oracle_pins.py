@@ -311,6 +311,17 @@ def test_skip_rule_two_cells_closed_form_and_adjoint():
     # a weight within 1e-4 relative of the threshold is flagged as ambiguous
     _, _, _, fl = O.render(sc, o[None], d[None], skip_weight=w1 * (1 + 5e-5), **kw)
     assert fl[0] != 0
+    # the test is on the weight T alpha, not on alpha: behind a dense first
+    # cell the second has alpha above the threshold but weight below it
+    sig1, sig2 = 2.0, 0.8
+    sc = O.OracleScene(np.stack([s1, s2]), [sig1, sig2], tex, [0, 1, 2], np.array([1, 0], np.int32))
+    e1, e2 = np.exp(-sig1 * d1), np.exp(-sig2 * d2)
+    w1, a2, w2 = 1 - e1, 1 - e2, e1 * (1 - e2)
+    skip = 0.2
+    assert w2 < skip < a2 and w1 > skip
+    rgb, Tout, _, flags = O.render(sc, o[None], d[None], skip_weight=skip, **kw)
+    assert flags[0] == 0
+    assert np.allclose(rgb[0], w1 * c1 + e1 * e2 * bg, atol=1e-14)
 
 
 def test_constant_texture_any_direction():
@@ -550,9 +561,18 @@ def test_concentric_map():
     for a, b in RNG.uniform(-1, 1, size=(300, 2)):
         r = np.linalg.norm(O.concentric(a, b))
         assert abs(r - max(abs(a), abs(b))) < 1e-14  # squares map to circles
-    # equal-area: uniform square samples -> uniform disk (mean r^2 = 1/2)
+    # equal-area: uniform square samples -> uniform disk (mean r^2 = 1/2) ...
     pts = np.array([O.concentric(a, b) for a, b in RNG.uniform(-1, 1, size=(20000, 2))])
     assert abs(np.mean(np.sum(pts ** 2, 1)) - 0.5) < 0.01
+    # ... with a uniform angle: each eighth of the disk gets an eighth of the samples
+    sector = np.floor((np.arctan2(pts[:, 1], pts[:, 0]) + np.pi) / (np.pi / 4)).astype(int) % 8
+    assert np.all(np.abs(np.bincount(sector, minlength=8) / len(pts) - 0.125) < 0.012)
+    # continuous across the square's diagonals, where the two wedges meet
+    for sa, sb in [(1, 1), (1, -1), (-1, 1), (-1, -1)]:
+        for r in (0.3, 1.0):
+            p = np.array(O.concentric(sa * r, sb * r * (1 - 1e-9)))
+            q = np.array(O.concentric(sa * r * (1 - 1e-9), sb * r))
+            assert np.allclose(p, q, atol=1e-8)
 
 
 def test_pinhole_rays():
