@@ -142,3 +142,61 @@ def test_every_planted_mistake_fails_a_pin(tmp_path):
     # exit code 1 = tests failed (a crash or an error in collection would not count)
     missed = [(what, rc, tail) for (what, _), (rc, tail) in zip(jobs[1:], results[1:]) if rc != 1]
     assert not missed, f"mistakes no pin caught: {missed}"
+
+
+# The numpy training helpers (oracle/training.py), mutated the same way and
+# checked in-process by the pins that cover them.
+TRAINING_SRC = os.path.join(ROOT, "oracle", "training.py")
+TRAINING_PINS = ["test_smooth_l1_matches_library", "test_adam_matches_library",
+                 "test_texture_regularizers_closed_forms_and_fd", "test_stratified_ray_sampling"]
+TRAINING_MUTANTS = [
+    ("Smooth-L1 linear branch offset by beta", "loss = np.where(small, 0.5 * r * r / beta, a - 0.5 * beta)",
+     "loss = np.where(small, 0.5 * r * r / beta, a - beta)"),
+    ("Smooth-L1 quadratic-branch gradient not divided by beta", "grad = np.where(small, r / beta, np.sign(r))",
+     "grad = np.where(small, r, np.sign(r))"),
+    ("Smooth-L1 gradient averaged over rays, not channels", "return loss.mean(), grad / r.size",
+     "return loss.mean(), grad / len(r)"),
+    ("regulariser normalised by N R, not N R^2", "scale = 1.0 / (n * R * R)", "scale = 1.0 / (n * R)"),
+    ("L_mean without the cell mean", "dev = t - mean[:, None, None, :]", "dev = t"),
+    ("L_mean gradient without its factor 2", "2.0 * lam_mean * scale * dev", "lam_mean * scale * dev"),
+    ("L_vd gradient with the other weight", "2.0 * lam_vd * scale * v", "2.0 * lam_mean * scale * v"),
+    ("Adam second moment of g, not g^2", "v = b2 * v + (1 - b2) * g * g", "v = b2 * v + (1 - b2) * np.abs(g)"),
+    ("Adam without bias correction of m", "mh = m / (1 - b1 ** step)", "mh = m"),
+    ("Adam epsilon inside the root", "p - lr * mh / (np.sqrt(vh) + eps)", "p - lr * mh / np.sqrt(vh + eps)"),
+    ("stratified samples not jittered", "i = int((k + uniform(seed, k)) * stride)", "i = int((k + 0.5) * stride)"),
+]
+
+
+def test_every_planted_training_mistake_fails_a_pin(monkeypatch):
+    import importlib.util
+
+    import oracle
+    import test_oracle_pins as pins
+
+    src = open(TRAINING_SRC).read()
+
+    def load(text, name):
+        spec = importlib.util.spec_from_loader(f"oracle.{name}", loader=None, origin=TRAINING_SRC)
+        mod = importlib.util.module_from_spec(spec)
+        mod.__package__ = "oracle"
+        exec(compile(text, TRAINING_SRC, "exec"), mod.__dict__)
+        return mod
+
+    def failures(mod):
+        monkeypatch.setattr(oracle, "training", mod, raising=False)
+        monkeypatch.setitem(sys.modules, "oracle.training", mod)
+        n = 0
+        for name in TRAINING_PINS:
+            try:
+                getattr(pins, name)()
+            except AssertionError:
+                n += 1
+        return n
+
+    assert failures(load(src, "training_unmutated")) == 0
+    missed = []
+    for k, (what, a, b) in enumerate(TRAINING_MUTANTS):
+        assert src.count(a) == 1, f"training mutant {k} ({what}): target text not found once"
+        if failures(load(src.replace(a, b), f"training_m{k}")) == 0:
+            missed.append(what)
+    assert not missed, f"mistakes no pin caught: {missed}"

@@ -1163,8 +1163,10 @@ def test_stratified_ray_sampling():
     k = np.arange(777)
     assert np.all(idx >= np.floor(k * stride)) and np.all(idx < np.ceil((k + 1) * stride))
     assert np.all(np.diff(idx) > 0)
-    # position inside the stratum is uniform: mean ~ 1/2
-    assert abs(np.mean((idx + 0.5) / stride - k) - 0.5) < 0.05
+    # position inside the stratum is uniform: mean ~ 1/2, variance ~ 1/12
+    pos = (idx + 0.5) / stride - k
+    assert abs(np.mean(pos) - 0.5) < 0.05
+    assert abs(np.var(pos) - 1.0 / 12.0) < 0.02
 
 
 # ---------------------------------------------------------------- stored expected values
