@@ -208,3 +208,24 @@ def test_api_rejects_tensors_the_kernels_cannot_take():
     with pytest.raises(ValueError, match="required"):
         api._arr(None, "x", (4, 3))
     api._arr(None, "x", (4, 3), optional=True)
+
+
+def test_oracle_and_cuda_path_share_no_code():
+    """The oracle includes only the C standard library and imports only numpy
+    and its own modules; the product package and the CUDA sources never name
+    the oracle. Only the seeded input generators (workloads.py) serve both."""
+    import glob
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    c_src = open(os.path.join(root, "oracle", "vt_oracle.c")).read()
+    assert set(re.findall(r'#include\s*[<"]([^>"]+)[>"]', c_src)) <= {"math.h", "pthread.h", "stdint.h", "stdlib.h",
+                                                                      "string.h"}
+    for f in glob.glob(os.path.join(root, "oracle", "*.py")):
+        mods = re.findall(r"^\s*(?:from|import)\s+([\w.]+)", open(f).read(), re.M)
+        assert all(m.split(".")[0] in {"__future__", "ctypes", "os", "subprocess", "numpy", "math"} or m == "."
+                   for m in mods), (f, mods)
+    product = glob.glob(os.path.join(root, "paper_2608_17682_gb300", "*.py")) + \
+        glob.glob(os.path.join(root, "paper_2608_17682_gb300", "csrc", "*")) + glob.glob(os.path.join(root, "include", "*"))
+    for f in product:
+        text = open(f, errors="replace").read()
+        assert not re.search(r"^\s*(from|import)\s+oracle|vt_oracle|libvt_oracle|\bvto_", text, re.M), f
