@@ -5,7 +5,7 @@
  * Method (arXiv 2608.17682, "Differentiable Voronoi Ray Tracing Beyond
  * Rasterization Speeds"):
  *   - Sec. 3.1: a ray starts in the Voronoi cell containing its origin (one
- *     nearest-site query) and walks from cell to cell through the nearest
+ *     nearest-site query) and steps to the next cell across the nearest
  *     forward bisector-plane crossing with the cell's Delaunay neighbours:
  *       t_j = n.((s_i+s_j)/2 - o) / (n.d),  n = s_j - s_i,  over n.d > 0.
  *   - Sec. 3.2: piecewise-constant volume rendering, alpha_k = 1 -
@@ -63,8 +63,8 @@ typedef enum {
   VT_ERR_UNSUPPORTED = 6  /* feature not available in this build                     */
 } vt_status;
 
-/* Storage precision of the octahedral textures (Sec. 5.6 "half-precision
- * appearance attributes"); compositing and accumulation are always FP32.
+/* Storage precision of the octahedral textures (Sec. 5.6 stores appearance in
+ * half precision); compositing and accumulation are always FP32.
  * FP16 and BF16 are rounded to nearest-even from the FP32 input. */
 typedef enum { VT_F32 = 0, VT_F16 = 1, VT_BF16 = 2 } vt_dtype;
 
