@@ -43,6 +43,14 @@ def to_dev(*a):
     return [torch.as_tensor(x, device=DEV).contiguous() for x in a]
 
 
+def seeded(*shape, seed, normal=True):
+    """Seeded random FP32 tensor on the device, drawn on the CPU so that it is
+    the same on every machine."""
+    g = torch.Generator().manual_seed(seed)
+    x = torch.randn(*shape, generator=g) if normal else torch.rand(*shape, generator=g)
+    return x.to(DEV)
+
+
 def fwd_res(scene, to, td, P):
     """Forward render that also returns the colour residual for the backward."""
     res = torch.empty(to.shape[0], 3, device=DEV)
@@ -231,7 +239,7 @@ def test_chunked_gradients_sum(medium):
     P1 = gpu_params(W.default_params())
     scene = api.Scene.from_workload(sc)
     to, td = to_dev(o, d)
-    g = torch.randn(len(o), 3, device=DEV)
+    g = seeded(len(o), 3, seed=101)
     rgb = api.render_fwd(scene, to, td, P1)[0]
     full = api.render_bwd(scene, to, td, P1, rgb, g)
     acc = [torch.zeros_like(x) for x in full]
@@ -266,8 +274,8 @@ def test_autograd_function(tiny):
 
 def test_l2_loss_kernel(tiny):
     wl, osc, o, d = tiny
-    rgb = torch.rand(4096, 3, device=DEV)
-    Y = torch.rand(4096, 3, device=DEV)
+    rgb = seeded(4096, 3, seed=102, normal=False)
+    Y = seeded(4096, 3, seed=103, normal=False)
     loss, grad = api.l2_loss(rgb, Y)
     r64 = (rgb.double() - Y.double())
     assert abs(loss.item() - (r64 ** 2).mean().item()) < 1e-6
@@ -296,10 +304,10 @@ def test_raygen_parity(kind):
 
 
 def test_average_samples():
-    x = torch.rand(40, 3, device=DEV)
+    x = seeded(40, 3, seed=104, normal=False)
     y = api.average_samples(x, 4)
     assert torch.allclose(y, x.view(10, 4, 3).mean(1), atol=1e-7)
-    g = torch.rand(10, 3, device=DEV)
+    g = seeded(10, 3, seed=105, normal=False)
     gx = api.average_samples_bwd(g, 4)
     assert torch.allclose(gx, g.repeat_interleave(4, 0) / 4, atol=1e-7)
 
@@ -457,7 +465,7 @@ def test_image_table_layout_matches_1d(medium):
     assert scene.get_error()[0] == 0
     for x, y in zip(a, b):
         assert torch.equal(x, y)
-    g = torch.randn(to.shape[0], 3, device=DEV)
+    g = seeded(to.shape[0], 3, seed=106)
     ga = api.render_bwd(scene, to, td, gpu_params(base, image_sizes=sizes), a[0], g)
     gb = api.render_bwd(scene, to, td, gpu_params(base), b[0], g)
     for x, y in zip(ga, gb):
@@ -761,7 +769,7 @@ def test_backward_scratch_is_clean_between_calls(medium):
     sc, osc, o, d, cams = medium
     P = gpu_params(W.default_params())
     to, td = to_dev(o, d)
-    g = torch.randn(len(o), 3, device=DEV)
+    g = seeded(len(o), 3, seed=107)
     used = api.Scene.from_workload(sc)
     rgb = api.render_fwd(used, to, td, P)[0]
     # dirty the scratch: a call without texel output, then one on half the rays
