@@ -38,7 +38,7 @@ METRIC = "Mrays/s fwd+bwd (FP16 textures)"
 HBM_FALLBACK_GBS = 6800.0
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -57,7 +57,44 @@ def parse():
     ap.add_argument("--ablation", action="store_true",
                     help="also time the forward pass with the inference-stack toggles (Morton order, 4x8 tiles, "
                          "cell skip 1e-3), cumulatively as in the paper's Sec. 6.3 ablation")
-    return ap.parse_args()
+    return ap.parse_args(argv)
+
+
+def metric_name(args):
+    """The metric of the line: Mrays/s fwd+bwd, named for the texture storage
+    type and the appearance model timed."""
+    m = METRIC if args.tex == "f16" else METRIC.replace("FP16", args.tex.upper())
+    return m + (", paper appearance model" if args.appearance else "")
+
+
+def workload_name(args, wl, cams):
+    """The workload one rank renders, by size (the `config.workload` key)."""
+    c0 = cams[0]
+    n_rays = sum(c.n_rays for c in cams)
+    return (f"{args.workload}: {wl.scene.n} sites, {wl.scene.R}x{wl.scene.R} {args.tex} textures"
+            f"{' (two maps, sigmoid)' if args.appearance else ''}, "
+            f"{len(cams)} x {c0.w}x{c0.h} cameras, {n_rays} rays/GPU")
+
+
+def appearance_maps(wl):
+    """Logit maps (T_vi, T_vd) of the paper's appearance model for the
+    workload, seed 5000+k."""
+    rng_app = np.random.default_rng(5000 + wl.seed)
+    tvd = rng_app.normal(0.0, 0.5, size=wl.scene.tex.shape).astype(np.float32)
+    tvi = rng_app.normal(0.0, 1.5, size=wl.scene.tex.shape).astype(np.float32)
+    return tvi, tvd
+
+
+def oracle_setup(args, wl):
+    """The oracle's copy of the timed scene and its render parameters."""
+    import oracle as O
+
+    if args.appearance:
+        tvi, tvd = appearance_maps(wl)
+        sc = wl.scene
+        return (O.OracleScene(sc.sites, sc.sigma, tvi, sc.offsets, sc.indices, tex_vd=tvd),
+                O.make_params(**wl.params, appearance=1))
+    return O.OracleScene.from_workload_scene(wl.scene), O.make_params(**wl.params)
 
 
 def dist_env():
@@ -201,9 +238,7 @@ def run_ours(args, ws, rank, local):
     Y = torch.as_tensor(W.target_image(n_rays, wl.seed), device=dev)
 
     # the paper's appearance model (Sec. 5.1-5.2): two maps of logits, sigmoid
-    rng_app = np.random.default_rng(5000 + wl.seed)
-    tvd = rng_app.normal(0.0, 0.5, size=wl.scene.tex.shape).astype(np.float32)
-    tvi = rng_app.normal(0.0, 1.5, size=wl.scene.tex.shape).astype(np.float32)
+    tvi, tvd = appearance_maps(wl)
 
     def make_scene(t, appearance, **kw):
         if appearance:
@@ -510,15 +545,12 @@ def run_ours(args, ws, rank, local):
             "ms_per_launch": round(ms_dom, 4)}
 
     line = {
-        "metric": (METRIC if args.tex == "f16" else METRIC.replace("FP16", args.tex.upper()))
-        + (", paper appearance model" if args.appearance else ""),
+        "metric": metric_name(args),
         "value": round(value * 1.0, 3), "unit": "Mrays/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
         "ms_per_step_median": round(walks["step_median"], 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {N} sites, {R}x{R} {args.tex} textures"
-                               f"{' (two maps, sigmoid)' if args.appearance else ''}, "
-                               f"{n_img} x {c0.w}x{c0.h} cameras, {n_rays} rays/GPU",
+        "config": {"workload": workload_name(args, wl, cams),
                    "global_batch": total_rays, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "flushed between timed steps (256 MB write outside the timed events)",
                    "scene_bytes": int(N * 32 + E * 16 + N * R * R * tb)},
@@ -529,7 +561,7 @@ def run_ours(args, ws, rank, local):
         "clocks": clk, "e2e": e2e, "gpu_launches": 9 * args.steps, "roofline": roof, **extra,
     }
     if rank == 0 and ws == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(wl, cams, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(args, wl, cams, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -566,11 +598,8 @@ def oracle_step(osc, o, d, Y, params):
     O.render_bwd(osc, o, d, g, params=params)
 
 
-def cpu_baseline(wl, cams, seconds):
-    import oracle as O
-
-    osc = O.OracleScene.from_workload_scene(wl.scene)
-    params = O.make_params(**wl.params)
+def cpu_baseline(args, wl, cams, seconds):
+    osc, params = oracle_setup(args, wl)
     n = 64
     while True:
         o, d = oracle_sample_rays(cams, n)
@@ -590,11 +619,8 @@ def cpu_baseline(wl, cams, seconds):
 def run_reference(args, ws, rank):
     if rank != 0:
         return
-    import oracle as O
-
     wl = W.make_workload(args.workload, n_sites=args.sites or None)
-    osc = O.OracleScene.from_workload_scene(wl.scene)
-    params = O.make_params(**wl.params)
+    osc, params = oracle_setup(args, wl)
     n = 256
     o, d = oracle_sample_rays(wl.cameras, n)
     Y = W.target_image(len(o), wl.seed)
@@ -605,10 +631,11 @@ def run_reference(args, ws, rank):
         oracle_step(osc, o, d, Y, params)
     dt = (time.time() - t) / args.steps
     v = len(o) / dt / 1e6
-    line = {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": "Mrays/s", "n_gpus": ws,
+    line = {"impl": "reference", "metric": metric_name(args), "value": round(v, 6), "unit": "Mrays/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {wl.scene.n} sites (oracle on a {len(o)}-ray sample per step)"},
+            "config": {"workload": workload_name(args, wl, rank_cameras(wl, 0)),
+                       "sample": f"the oracle times a {len(o)}-ray strided sample of these rays per step"},
             "cpu_baseline": {"value": round(v, 6), "unit": "Mrays/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"{len(o)} rays strided over the views per step"},
             "e2e": {"value": round(v, 6), "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -170,6 +170,14 @@ def test_reference_arm_json_line():
     assert j["cpu_baseline"]["kind"] == "oracle" and j["cpu_baseline"]["value"] == j["value"]
     assert j["e2e"]["h2d_bytes_per_step"] == 0 and j["e2e"]["d2h_bytes_per_step"] == 0
     assert j["steps"] == 1 and j["warmup"] == 1 and j["n_gpus"] == 1
+    # the same metric and workload names as the CUDA arm's line
+    sys.path.insert(0, root)
+    import bench
+    from paper_2608_17682_gb300 import workloads as W
+    args = bench.parse(["--workload", "tiny"])
+    wl = W.make_workload("tiny")
+    assert j["metric"] == bench.metric_name(args)
+    assert j["config"]["workload"] == bench.workload_name(args, wl, bench.rank_cameras(wl, 0))
 
 
 def test_api_rejects_tensors_the_kernels_cannot_take():
