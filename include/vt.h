@@ -166,7 +166,9 @@ vt_status vt_scene_info(const vt_scene* s, int64_t* n_sites, int32_t* tex_res, i
  * scene since the last call (VT_ERR_MAX_STEPS, VT_ERR_CAPACITY) or VT_OK,
  * and clear it. Also returns VT_ERR_CUDA for an asynchronous CUDA fault.
  * If n_fp64 is not NULL it receives the number of FP64 plane rechecks done
- * since the last call (grazing planes with |n.d| < 1e-6 |n| |d|). */
+ * since the last call: planes of a walked cell with |n.d| <= 1e-6 |d| max|n|,
+ * the maximum over that cell's neighbours (a superset of the planes with
+ * |n.d| <= 1e-6 |n| |d|). */
 vt_status vt_scene_get_error(vt_scene* s, void* stream, int64_t* n_fp64);
 
 /* ---------------------------------------------------------------------- */
