@@ -105,6 +105,15 @@ MUTANTS = [
     ("interval-end derivative dropped", "if (a->b == a->t_out && a->t_out < t1) xterm[k] += dLdb;", ""),
     ("ordering sign of the midpoints flipped", "(sk > sl ? 1.0 : (sk < sl ? -1.0 : 0.0))",
      "(sk > sl ? -1.0 : (sk < sl ? 1.0 : 0.0))"),
+    # readings of ties and camera conventions
+    ("nearest-site ties to the higher id", "if (dd < bd) {\n      bd = dd;", "if (dd <= bd) {\n      bd = dd;"),
+    ("exact exit ties to the later CSR entry", "if (t < best_t) {", "if (t <= best_t) {"),
+    ("fisheye azimuth axes swapped", "double cp = rr > 0.0 ? px / rr : 1.0, sp = rr > 0.0 ? py / rr : 0.0;",
+     "double cp = rr > 0.0 ? py / rr : 1.0, sp = rr > 0.0 ? px / rr : 0.0;"),
+    ("camera basis mirrored", "cross3(f, c->up, r);", "cross3(c->up, f, r);"),
+    ("rolling-shutter origin fixed at mid-frame",
+     "tm = (double)y / (double)c->h;\n            for (int k = 0; k < 3; ++k) oo[k] += tm * c->rs_velocity[k];",
+     "tm = (double)y / (double)c->h;\n            for (int k = 0; k < 3; ++k) oo[k] += 0.5 * c->rs_velocity[k];"),
 ]
 
 

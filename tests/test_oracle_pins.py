@@ -108,6 +108,31 @@ def test_nearest_matches_kdtree():
         assert O.nearest(s, q) == tree.query(q)[1]
 
 
+def test_nearest_ties_go_to_the_lower_id():
+    """Start-cell reading: a point equidistant from two sites (exactly, in
+    binary) belongs to the site with the lower index."""
+    s = np.array([[0.0, 0.0, 0.0], [2.0, 0.0, 0.0], [1.0, 5.0, 0.0]])
+    q = [1.0, 0.3, -0.2]
+    assert O.nearest(s, q) == 0
+    assert O.nearest(s[[1, 0, 2]], q) == 0
+
+
+def test_exact_exit_ties_keep_the_earlier_csr_entry():
+    """Exit reading: when two bisector planes give the same crossing t (the
+    ray leaves through a Voronoi edge), the neighbour listed first in the
+    cell's adjacency row is taken."""
+    s = np.array([[0.0, 0.0, 0.0], [2.0, 0.0, 0.0], [0.0, 2.0, 0.0]])
+    tex = np.full((3, 2, 2, 3), 0.5)
+    o = np.array([0.25, 0.25, 0.0])
+    d = np.array([1.0, 1.0, 0.0]) / math.sqrt(2.0)
+    for row0 in ([1, 2], [2, 1]):
+        idx = np.array(row0 + [0, 2, 0, 1], np.int32)
+        sc = O.OracleScene(s, [1.0, 1.0, 1.0], tex, [0, 2, 4, 6], idx)
+        cells, t_out, n, _ = O.trace(sc, o[None], d[None], max_cells=4, t_far=3.0, T_eps=0.0)
+        assert cells[0, 0] == 0 and cells[0, 1] == row0[0], (row0, cells[0])
+        assert abs(t_out[0, 0] - 0.75 * math.sqrt(2.0)) < 1e-15
+
+
 # ---------------------------------------------------------------- walk + compositing
 
 @pytest.fixture(scope="module")
@@ -602,6 +627,18 @@ def test_fisheye_equidistant():
             rpx = math.hypot(x + 0.5 - 20, 15 - (y + 0.5))
             theta = math.acos(np.clip(img[y, x] @ f, -1, 1))
             assert abs(theta - rpx / (20 / (math.pi / 2))) < 1e-12
+    # azimuth: a ray bends towards its pixel's offset from the image centre,
+    # measured in the camera's right / up axes (right = f x up, up' = right x f)
+    up = np.asarray(cam.up, float)
+    right = np.cross(f, up)
+    right /= np.linalg.norm(right)
+    upc = np.cross(right, f)
+    for y in range(30):
+        for x in range(40):
+            px, py = x + 0.5 - 20, 15 - (y + 0.5)
+            az = math.atan2(img[y, x] @ upc, img[y, x] @ right)
+            diff = (az - math.atan2(py, px) + math.pi) % (2 * math.pi) - math.pi
+            assert abs(diff) < 1e-9, (x, y)
 
 
 def test_rolling_shutter():
