@@ -111,6 +111,29 @@ MUTANTS = [
     ("fisheye azimuth axes swapped", "double cp = rr > 0.0 ? px / rr : 1.0, sp = rr > 0.0 ? py / rr : 0.0;",
      "double cp = rr > 0.0 ? py / rr : 1.0, sp = rr > 0.0 ? px / rr : 0.0;"),
     ("camera basis mirrored", "cross3(f, c->up, r);", "cross3(c->up, f, r);"),
+    ("camera basis: wrong sign in a cross product", "c[0] = a[1] * b[2] - a[2] * b[1];",
+     "c[0] = a[1] * b[2] + a[2] * b[1];"),
+    ("pinhole aspect ratio inverted", "tx = ty * (double)c->w / (double)c->h;",
+     "tx = ty / (double)c->w / (double)c->h;"),
+    ("pinhole image mirrored", "for (int k = 0; k < 3; ++k) pd[k] = f[k] + px * r[k] + py * u[k];",
+     "for (int k = 0; k < 3; ++k) pd[k] = f[k] - px * r[k] + py * u[k];"),
+    # routing of gradients and the band test
+    ("no site gradient at crossings into cell 0", "if (j < 0 || !isfinite(tb)) continue;",
+     "if (j <= 0 || !isfinite(tb)) continue;"),
+    ("first texel's gradient routed to a density", "else if (i < n4)\n", "else if (i <= n4)\n"),
+    ("first view-dependent texel's gradient routed to the other map", "else if (i < nt)\n", "else if (i <= nt)\n"),
+    ("distortion weight derivative divides by the distance", "dw += 2.0 * b->w * fabs(sk - sl);",
+     "dw += 2.0 * b->w / fabs(sk - sl);"),
+    ("band test: wrong plane normal", "double n[3] = {sb[0] - sa[0], sb[1] - sa[1], sb[2] - sa[2]};",
+     "double n[3] = {sb[0] - sa[0], sb[1] - sa[1], sb[2] + sa[2]};"),
+    ("band test: wrong plane midpoint",
+     "double m[3] = {0.5 * (sa[0] + sb[0]), 0.5 * (sa[1] + sb[1]), 0.5 * (sa[2] + sb[2])};",
+     "double m[3] = {0.5 * (sa[0] + sb[0]), 0.25 * (sa[1] + sb[1]), 0.5 * (sa[2] + sb[2])};"),
+    ("band test: origin checked against the wrong site",
+     "if (plane_dist(sc->sites + 3 * cell, sc->sites + 3 * (int64_t)sc->idx[q], o) < p->band_eps)",
+     "if (plane_dist(sc->sites - 3 * cell, sc->sites + 3 * (int64_t)sc->idx[q], o) < p->band_eps)"),
+    ("band test: wrong segment end point", "double xe[3] = {o[0] + te * d[0], o[1] + te * d[1], o[2] + te * d[2]};",
+     "double xe[3] = {o[0] + te * d[0], o[1] - te * d[1], o[2] + te * d[2]};"),
     ("rolling-shutter origin fixed at mid-frame",
      "tm = (double)y / (double)c->h;\n            for (int k = 0; k < 3; ++k) oo[k] += tm * c->rs_velocity[k];",
      "tm = (double)y / (double)c->h;\n            for (int k = 0; k < 3; ++k) oo[k] += 0.5 * c->rs_velocity[k];"),

@@ -18,6 +18,14 @@ from paper_2608_17682_gb300 import workloads as W
 RNG = np.random.default_rng(12345)
 
 
+def _fd_ok(fd, an, floor):
+    """Central difference `fd` against the analytic derivative `an` at 1e-4
+    relative (floor `floor`). All three must be finite: an infinite analytic
+    value or floor would otherwise pass its own relative bound."""
+    return (math.isfinite(fd) and math.isfinite(an) and math.isfinite(floor)
+            and abs(fd - an) <= 1e-4 * max(abs(an), floor))
+
+
 # ---------------------------------------------------------------- octahedral map (Sec. 5.1)
 
 def _oct_inverse(u, v):
@@ -349,6 +357,61 @@ def test_skip_rule_two_cells_closed_form_and_adjoint():
     assert np.allclose(rgb[0], w1 * c1 + e1 * e2 * bg, atol=1e-14)
 
 
+def test_two_cell_site_gradients_both_ways():
+    """dL/ds of both sites through the plane crossing, against central
+    differences of the forward pass, for a ray from cell 0 into cell 1 and
+    for one from cell 1 into cell 0 (with different colours and densities)."""
+    s = np.array([[0.0, 0.0, 0.0], [1.0, 0.2, -0.1]])
+    tex = np.stack([np.broadcast_to([1.0, 0.2, 0.1], (4, 4, 3)), np.broadcast_to([0.1, 0.3, 1.0], (4, 4, 3))])
+    sig = [0.9, 2.5]
+    adj = ([0, 1, 2], np.array([1, 0], np.int32))
+    g = np.array([0.7, -1.3, 0.4])
+    kw = dict(t_far=4.0, T_eps=0.0, bg=(0.2, 0.4, 0.6))
+    for o, d in ((np.array([-1.0, 0.05, 0.02]), np.array([1.0, 0.1, 0.0])),
+                 (np.array([2.0, 0.3, 0.1]), np.array([-1.0, -0.05, 0.03]))):
+        d = d / np.linalg.norm(d)
+        gs, _, _ = O.render_bwd(O.OracleScene(s, sig, tex, *adj), o[None], d[None], g[None], **kw)
+        assert np.abs(gs).max() > 1e-3  # a non-trivial gradient to check
+        h = 1e-6
+        for i in range(2):
+            for k in range(3):
+                sp, sm = s.copy(), s.copy()
+                sp[i, k] += h
+                sm[i, k] -= h
+                fp = O.render(O.OracleScene(sp, sig, tex, *adj), o[None], d[None], **kw)[0][0]
+                fm = O.render(O.OracleScene(sm, sig, tex, *adj), o[None], d[None], **kw)[0][0]
+                fd = g @ (fp - fm) / (2 * h)
+                assert _fd_ok(fd, gs[i, k], 1e-3 * np.abs(gs).max()), (o, i, k, fd, gs[i, k])
+
+
+def test_texel_gradients_reach_the_first_texel():
+    """One cell, a ray whose bilinear taps sit in the octahedral corner
+    (-1,-1): all of w g lands on texel (0,0) of cell 0. With the paper's
+    model, a view direction -d in that corner sends w g c (1 - c) to texel
+    (0,0) of the view-dependent map."""
+    R, sig, L = 4, 1.3, 0.8
+    w = 1 - math.exp(-sig * L)
+    g = np.array([0.7, -0.4, 0.2])
+    c = np.array([0.3, 0.6, 0.9])
+    tex = np.broadcast_to(c, (1, R, R, 3)).copy()
+    d = np.array([-0.01, -0.01, -1.0])
+    d /= np.linalg.norm(d)
+    kw = dict(t_far=L, T_eps=0.0, bg=(0.0, 0.0, 0.0))
+    sc = O.OracleScene(np.zeros((1, 3)), [sig], tex, [0, 0], np.zeros(0, np.int32))
+    _, gsig, gt = O.render_bwd(sc, np.zeros((1, 3)), d[None], g[None], **kw)
+    expect = np.zeros((1, R, R, 3))
+    expect[0, 0, 0] = w * g
+    assert np.allclose(gt, expect, rtol=0, atol=1e-15)
+    assert abs(gsig[0] - (g @ c) * L * math.exp(-sig * L)) < 1e-14
+    tvd = np.broadcast_to([0.1, -0.2, 0.3], (1, R, R, 3)).copy()
+    sc = O.OracleScene(np.zeros((1, 3)), [sig], tex, [0, 0], np.zeros(0, np.int32), tex_vd=tvd)
+    _, _, _, gvd = O.render_bwd(sc, np.zeros((1, 3)), -d[None], g[None], appearance=1, **kw)
+    cc = 1 / (1 + np.exp(-(c + tvd[0, 0, 0])))
+    expect = np.zeros((1, R, R, 3))
+    expect[0, 0, 0] = w * g * cc * (1 - cc)
+    assert np.allclose(gvd, expect, rtol=0, atol=1e-15)
+
+
 def test_constant_texture_any_direction():
     c = np.array([0.25, 0.5, 0.75])
     sc = _one_site_scene([0, 0, 0], 3.0, c, R=8)
@@ -450,6 +513,30 @@ def test_band_flags_edge_ray():
     o2[1] = cc[1] + 0.25  # away from the edge
     _, _, _, fl2 = O.render(sc, o2[None], d[None], t_far=5.0, T_eps=0.0)
     assert fl2[0] & O.F_NEAR_EDGE == 0
+    # the same configuration turned and moved in space: the flags do not
+    # depend on the axes (every coordinate of the test enters)
+    Q, _ = np.linalg.qr(np.random.default_rng(21).normal(size=(3, 3)))
+    shift = np.array([0.3, -0.7, 1.1])
+    scq = O.OracleScene(s @ Q.T + shift, [1.0] * 5, tex, ip, ind)
+    _, _, _, fq = O.render(scq, (Q @ o + shift)[None], (Q @ d)[None], t_far=5.0, T_eps=0.0)
+    _, _, _, fq2 = O.render(scq, (Q @ o2 + shift)[None], (Q @ d)[None], t_far=5.0, T_eps=0.0)
+    assert fq[0] & O.F_NEAR_EDGE and fq2[0] & O.F_NEAR_EDGE == 0
+
+
+def test_band_flag_for_an_origin_next_to_a_face():
+    """An origin within band_eps (1e-6) of a bisector plane of its cell is
+    flagged; one 5e-6 away is not. Two sites in general position."""
+    s = np.array([[0.1, 0.2, 0.3], [0.9, 0.5, -0.2]])
+    tex = np.full((2, 2, 2, 3), 0.5)
+    sc = O.OracleScene(s, [1.0, 1.0], tex, [0, 1, 2], np.array([1, 0], np.int32))
+    n = (s[1] - s[0]) / np.linalg.norm(s[1] - s[0])
+    tang = np.cross(n, [0.3, -0.4, 0.8])
+    foot = 0.5 * (s[0] + s[1]) + 0.2 * tang / np.linalg.norm(tang)
+    d = np.array([[0.2, 0.9, 0.3]])
+    for side in (-1.0, 1.0):  # origins in the cell of site 0, then of site 1
+        for dist, flagged in ((0.5e-6, True), (5e-6, False)):
+            _, _, _, fl = O.render(sc, (foot + side * dist * n)[None], d, t_far=1.0, T_eps=0.0)
+            assert bool(fl[0] & O.F_NEAR_ORIGIN) == flagged, (side, dist)
 
 
 def test_max_steps_flag(tiny):
@@ -561,7 +648,7 @@ def test_fd_site_positions(fd_setup):
         if not same:
             continue  # perturbation changes a cell sequence: no derivative there
         fd = (vals[0] - vals[1]) / (2 * h)
-        assert abs(fd - gs[i, c]) <= 1e-4 * max(abs(gs[i, c]), 1e-3 * np.abs(gs).max()), (i, c, fd, gs[i, c])
+        assert _fd_ok(fd, gs[i, c], 1e-3 * np.abs(gs).max()), (i, c, fd, gs[i, c])
         checked += 1
         if checked >= 25:
             break
@@ -615,6 +702,27 @@ def test_pinhole_rays():
     assert abs(ang - 2 * math.atan((1 - 1 / 48) * math.tan(math.radians(25)))) < 1e-3
     # image "up" is world +z-ish: top rows look higher than bottom rows
     assert img[0, 32, 2] > img[47, 32, 2]
+
+
+def test_pinhole_basis_with_a_tilted_up_vector():
+    """Camera frame f = fwd/|fwd|, right = f x up (normalised), up' = right x f,
+    for an up vector off every axis: the centre pixel looks along f, the
+    centre row stays in the (f, right) plane and the centre column in the
+    (f, up') plane, right/top edges lean towards +right/+up', and the
+    horizontal field of view follows from the vertical one and the aspect."""
+    w, h, fov = 31, 21, math.radians(50)
+    cam = W.look_at_camera(0, w, h, (2.0, -1.5, 0.7), (0.1, 0.2, -0.3), up=(0.3, 0.2, 1.0), fov_y=fov)
+    _, d, _ = O.raygen(cam)
+    img = d.reshape(h, w, 3)
+    f = np.asarray(cam.fwd) / np.linalg.norm(cam.fwd)
+    right = np.cross(f, cam.up)
+    right /= np.linalg.norm(right)
+    upc = np.cross(right, f)
+    assert np.allclose(img[h // 2, w // 2], f, atol=1e-15)
+    assert np.abs(img[h // 2] @ upc).max() < 1e-15 and np.abs(img[:, w // 2] @ right).max() < 1e-15
+    assert img[h // 2, -1] @ right > 0 and img[0, w // 2] @ upc > 0
+    ang = math.acos(np.clip(img[h // 2, 0] @ img[h // 2, -1], -1, 1))
+    assert abs(ang - 2 * math.atan((1 - 1 / w) * math.tan(fov / 2) * w / h)) < 1e-12
 
 
 def test_fisheye_equidistant():
@@ -810,7 +918,7 @@ def test_fd_on_surface_crop():
     kinds = [r[0] for r in res]
     assert kinds.count("sites") >= 15 and kinds.count("sigma") == 20 and kinds.count("tex") == 20
     for kind, idx, fd, an in res:
-        assert abs(fd - an) <= 1e-4 * max(abs(an), floors[kind]), (kind, idx, fd, an)
+        assert _fd_ok(fd, an, floors[kind]), (kind, idx, fd, an)
 
 
 # ---------------------------------------------------------------- appearance model of Sec. 5.1-5.2
@@ -884,7 +992,7 @@ def test_fd_paper_appearance_on_surface_crop():
         return 0.5 * np.sum((O.render(sc2, o, d, params=p, n_threads=1)[0] - Y) ** 2), sc2
 
     def check(fd, an, scale):
-        assert abs(fd - an) <= 1e-4 * max(abs(an), 1e-3 * scale), (fd, an)
+        assert _fd_ok(fd, an, 1e-3 * scale), (fd, an)
 
     for arr, g, name in ((tex_vi, gt, "vi"), (tex_vd, gtv, "vd")):
         cand = np.argwhere(np.abs(g) > 1e-9)
@@ -961,7 +1069,7 @@ def test_fd_paper_appearance_rays_starting_inside():
             if v is None:
                 continue
             fd = (v[0] - v[1]) / 2e-7
-            assert abs(fd - gs[i, k]) <= 1e-4 * max(abs(gs[i, k]), 1e-3 * np.abs(gs).max()), (i, k, fd, gs[i, k])
+            assert _fd_ok(fd, gs[i, k], 1e-3 * np.abs(gs).max()), (i, k, fd, gs[i, k])
             checked += 1
         if checked >= 12:
             break
@@ -1090,7 +1198,7 @@ def test_fd_distortion_on_surface_crop():
     res = _crop_dist_fd(params)
     assert sum(r[0] == "sites" for r in res) >= 10
     for kind, fd, an, mx in res:
-        assert abs(fd - an) <= 1e-4 * max(abs(an), 1e-3 * mx), (kind, fd, an)
+        assert _fd_ok(fd, an, 1e-3 * mx), (kind, fd, an)
 
 
 def test_distortion_gradient_adds_to_colour_gradient(tiny):
@@ -1294,7 +1402,7 @@ def test_fd_distortion_rays_starting_inside_with_termination():
             sg[i] += sgn * h
             v.append(F(sigma=sg)[0])
         fd = (v[0] - v[1]) / (2 * h)
-        assert abs(fd - gsig[i]) <= 1e-4 * max(abs(gsig[i]), 1e-3 * np.abs(gsig).max()), (i, fd, gsig[i])
+        assert _fd_ok(fd, gsig[i], 1e-3 * np.abs(gsig).max()), (i, fd, gsig[i])
     checked = 0
     for q in np.argwhere(np.abs(gs) > 1e-9)[rng.permutation(int((np.abs(gs) > 1e-9).sum()))]:
         i, k = int(q[0]), int(q[1])
@@ -1309,7 +1417,7 @@ def test_fd_distortion_rays_starting_inside_with_termination():
         if len(v) < 2:
             continue
         fd = (v[0] - v[1]) / 2e-7
-        assert abs(fd - gs[i, k]) <= 1e-4 * max(abs(gs[i, k]), 1e-3 * np.abs(gs).max()), (i, k, fd, gs[i, k])
+        assert _fd_ok(fd, gs[i, k], 1e-3 * np.abs(gs).max()), (i, k, fd, gs[i, k])
         checked += 1
         if checked >= 12:
             break
