@@ -134,6 +134,17 @@ MUTANTS = [
      "if (plane_dist(sc->sites - 3 * cell, sc->sites + 3 * (int64_t)sc->idx[q], o) < p->band_eps)"),
     ("band test: wrong segment end point", "double xe[3] = {o[0] + te * d[0], o[1] + te * d[1], o[2] + te * d[2]};",
      "double xe[3] = {o[0] + te * d[0], o[1] - te * d[1], o[2] + te * d[2]};"),
+    ("band test: segment end checked against the wrong neighbour",
+     "if (plane_dist(si, sc->sites + 3 * j, xe) < p->band_eps) {", "if (plane_dist(si, sc->sites - 3 * j, xe) < p->band_eps) {"),
+    ("band test: crossing near t_far never seen",
+     "(fabs(best_t - t1) < p->band_eps || fabs(best_t - t0) < p->band_eps)",
+     "(fabs(best_t + t1) < p->band_eps || fabs(best_t - t0) < p->band_eps)"),
+    ("band test: crossing near t_near never seen",
+     "(fabs(best_t - t1) < p->band_eps || fabs(best_t - t0) < p->band_eps)",
+     "(fabs(best_t - t1) < p->band_eps || fabs(best_t + t0) < p->band_eps)"),
+    ("band test: origin checked against the wrong neighbour",
+     "if (plane_dist(sc->sites + 3 * cell, sc->sites + 3 * (int64_t)sc->idx[q], o) < p->band_eps)",
+     "if (plane_dist(sc->sites + 3 * cell, sc->sites - 3 * (int64_t)sc->idx[q], o) < p->band_eps)"),
     ("rolling-shutter origin fixed at mid-frame",
      "tm = (double)y / (double)c->h;\n            for (int k = 0; k < 3; ++k) oo[k] += tm * c->rs_velocity[k];",
      "tm = (double)y / (double)c->h;\n            for (int k = 0; k < 3; ++k) oo[k] += 0.5 * c->rs_velocity[k];"),

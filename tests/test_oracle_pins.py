@@ -513,14 +513,39 @@ def test_band_flags_edge_ray():
     o2[1] = cc[1] + 0.25  # away from the edge
     _, _, _, fl2 = O.render(sc, o2[None], d[None], t_far=5.0, T_eps=0.0)
     assert fl2[0] & O.F_NEAR_EDGE == 0
-    # the same configuration turned and moved in space: the flags do not
-    # depend on the axes (every coordinate of the test enters)
+    # the same configuration turned, moved and relabelled: the flags depend
+    # neither on the axes nor on the site ids
     Q, _ = np.linalg.qr(np.random.default_rng(21).normal(size=(3, 3)))
     shift = np.array([0.3, -0.7, 1.1])
-    scq = O.OracleScene(s @ Q.T + shift, [1.0] * 5, tex, ip, ind)
+    sq = (s @ Q.T + shift)[[4, 2, 3, 0, 1]]
+    ipq, indq = Delaunay(sq).vertex_neighbor_vertices
+    scq = O.OracleScene(sq, [1.0] * 5, tex, ipq, indq)
     _, _, _, fq = O.render(scq, (Q @ o + shift)[None], (Q @ d)[None], t_far=5.0, T_eps=0.0)
     _, _, _, fq2 = O.render(scq, (Q @ o2 + shift)[None], (Q @ d)[None], t_far=5.0, T_eps=0.0)
     assert fq[0] & O.F_NEAR_EDGE and fq2[0] & O.F_NEAR_EDGE == 0
+
+
+def test_band_flag_for_a_crossing_next_to_the_clip_ends():
+    """A plane crossing within band_eps of t_near or t_far is flagged; one 5e-6
+    away is not (two sites in general position, crossing at t*)."""
+    s = np.array([[0.1, 0.2, 0.3], [0.9, 0.5, -0.2]])
+    tex = np.full((2, 2, 2, 3), 0.5)
+    sc = O.OracleScene(s, [1.0, 1.0], tex, [0, 1, 2], np.array([1, 0], np.int32))
+    o = np.array([-0.4, 0.1, 0.5])
+    n = s[1] - s[0]
+    # a unit direction, and a long one (|d| = 3) nearly along n, for which a
+    # t-gap of 0.5e-6 puts the ray end 1.5e-6 from the plane: the band is
+    # measured in t
+    unit = np.array([0.9, 0.3, -0.2]) / np.linalg.norm([0.9, 0.3, -0.2])
+    along = n / np.linalg.norm(n) + [0.0, 0.05, 0.02]
+    for d in (unit, 3.0 * along / np.linalg.norm(along)):
+        tstar = n @ (0.5 * (s[0] + s[1]) - o) / (n @ d)
+        assert O.nearest(s, o) == 0 and tstar > 0.1
+        for gap, flagged in ((0.5e-6, True), (5e-6, False)):
+            for kw in (dict(t_far=tstar + gap), dict(t_far=tstar - gap), dict(t_near=tstar - gap, t_far=5.0),
+                       dict(t_near=tstar + gap, t_far=5.0)):
+                _, _, _, fl = O.render(sc, o[None], d[None], T_eps=0.0, **kw)
+                assert bool(fl[0] & O.F_NEAR_CLIP) == flagged, (gap, kw)
 
 
 def test_band_flag_for_an_origin_next_to_a_face():
