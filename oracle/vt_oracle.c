@@ -49,6 +49,8 @@
  * Parity pins for every function live in tests/test_oracle_pins.py; the
  * skip_weight > 0 rule (Sec. 5.6: below the threshold a cell attenuates T but
  * adds no colour) is pinned by a two-cell closed form of colour and adjoint.
+ * tests/test_oracle_mutations.py compiles copies of this file, each with one
+ * plausible mistake planted, and checks that the pins fail on every copy.
  */
 #include <math.h>
 #include <pthread.h>
