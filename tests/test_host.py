@@ -237,3 +237,22 @@ def test_oracle_and_cuda_path_share_no_code():
     for f in product:
         text = open(f, errors="replace").read()
         assert not re.search(r"^\s*(from|import)\s+oracle|vt_oracle|libvt_oracle|\bvto_", text, re.M), f
+
+
+def test_density_and_texture_recipes():
+    """The stated input recipe: uniform scenes with sigma = exp(N(0, 1.5^2)),
+    surface scenes with exp(N(3,1)) on the 70% surface sites and exp(N(-2,1))
+    elsewhere, textures U[0,1]."""
+    from paper_2608_17682_gb300 import workloads as W
+    sc = W.make_scene("uniform", 4000, 4, 11)
+    ls = np.log(sc.sigma.astype(np.float64))
+    assert abs(ls.mean()) < 0.1 and abs(ls.std() - 1.5) < 0.1
+    assert np.all((sc.sites >= 0) & (sc.sites <= 1))
+    assert sc.tex.min() >= 0 and sc.tex.max() <= 1 and abs(sc.tex.mean() - 0.5) < 0.01
+    sc = W.make_scene("surface", 20000, 4, 12)
+    ls = np.log(sc.sigma.astype(np.float64))
+    # a two-component mixture: 0.7 N(3,1) + 0.3 N(-2,1)
+    assert abs(ls.mean() - (0.7 * 3.0 + 0.3 * -2.0)) < 0.05
+    from math import erf, sqrt
+    above = 0.7 * 0.5 * (1 + erf(2.5 / sqrt(2))) + 0.3 * 0.5 * (1 - erf(2.5 / sqrt(2)))
+    assert abs((ls > 0.5).mean() - above) < 0.01
