@@ -302,4 +302,4 @@ def test_plain_c_client_compiles_links_and_calls_the_abi(vt, tmp_path):
     t_near, t_far, T_eps, app, n_rays, ok, err = out.stdout.split()
     assert (float(t_near), float(t_far), float(T_eps), int(app)) == (0.0, 20.0, 1e-4, 0)
     assert int(n_rays) == 12 * 10 * 4
-    assert ok != err  # a NULL scene is rejected with a status, not a crash
+    assert ok == "VT_OK" and err == "VT_ERR_INVALID_ARG"  # a NULL scene is rejected on the host
