@@ -303,3 +303,12 @@ def test_plain_c_client_compiles_links_and_calls_the_abi(vt, tmp_path):
     assert (float(t_near), float(t_far), float(T_eps), int(app)) == (0.0, 20.0, 1e-4, 0)
     assert int(n_rays) == 12 * 10 * 4
     assert ok == "VT_OK" and err == "VT_ERR_INVALID_ARG"  # a NULL scene is rejected on the host
+
+
+def test_missing_library_fails_loudly():
+    """Without libvt.so the package raises on import: there is no CPU
+    fallback for the renderer."""
+    env = dict(os.environ, VT_LIB_PATH=os.path.join(ROOT, "no-such-dir", "libvt.so"))
+    out = subprocess.run([sys.executable, "-c", "from paper_2608_17682_gb300 import api"], cwd=ROOT, env=env,
+                         capture_output=True, text=True, timeout=300)
+    assert out.returncode != 0 and "ImportError" in out.stderr and "no CPU fallback" in out.stderr
