@@ -145,6 +145,14 @@ MUTANTS = [
     ("band test: origin checked against the wrong neighbour",
      "if (plane_dist(sc->sites + 3 * cell, sc->sites + 3 * (int64_t)sc->idx[q], o) < p->band_eps)",
      "if (plane_dist(sc->sites + 3 * cell, sc->sites - 3 * (int64_t)sc->idx[q], o) < p->band_eps)"),
+    ("termination band widened to 1e-2", "if (fabs(T / p->T_eps - 1.0) < 1e-4) *flags |= VTO_F_T_AMBIG;",
+     "if (fabs(T / p->T_eps - 1.0) < 1e-2) *flags |= VTO_F_T_AMBIG;"),
+    ("termination band narrowed to 1e-6", "if (fabs(T / p->T_eps - 1.0) < 1e-4) *flags |= VTO_F_T_AMBIG;",
+     "if (fabs(T / p->T_eps - 1.0) < 1e-6) *flags |= VTO_F_T_AMBIG;"),
+    ("termination band read on T before the cell",
+     "T = T * e;\n      if (fabs(T / p->T_eps - 1.0) < 1e-4) *flags |= VTO_F_T_AMBIG;",
+     "if (fabs(T / p->T_eps - 1.0) < 1e-4) *flags |= VTO_F_T_AMBIG;\n      T = T * e;"),
+    ("termination band never flagged", "if (fabs(T / p->T_eps - 1.0) < 1e-4) *flags |= VTO_F_T_AMBIG;", ""),
     ("rolling-shutter origin fixed at mid-frame",
      "tm = (double)y / (double)c->h;\n            for (int k = 0; k < 3; ++k) oo[k] += tm * c->rs_velocity[k];",
      "tm = (double)y / (double)c->h;\n            for (int k = 0; k < 3; ++k) oo[k] += 0.5 * c->rs_velocity[k];"),

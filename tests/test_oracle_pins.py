@@ -564,6 +564,52 @@ def test_band_flag_for_an_origin_next_to_a_face():
             assert bool(fl[0] & O.F_NEAR_ORIGIN) == flagged, (side, dist)
 
 
+def test_band_flag_for_an_ambiguous_termination():
+    """Early termination (Sec. 3.2) stops after the cell that brings T below
+    T_eps. Where T after a cell lies within 1e-4 relative of T_eps, FP32 and
+    FP64 may stop at different cells, so the ray is flagged F_T_AMBIG; 5e-3
+    away it is not. Two cells with closed-form transmittances: T = 1 before
+    the first cell, e1 = exp(-sigma_1 t*) after it and e1 e2 after the second.
+    The flag must read T after compositing a cell: a T_eps next to the final
+    e1 e2 (which no T before a cell equals) is flagged, one next to the initial
+    T = 1 is not."""
+    s1, s2 = np.array([0.0, 0.0, 0.0]), np.array([1.0, 0.2, -0.1])
+    tex = np.full((2, 4, 4, 3), 0.5)
+    sig1, sig2 = 0.9, 2.5
+    sc = O.OracleScene(np.stack([s1, s2]), [sig1, sig2], tex, [0, 1, 2], np.array([1, 0], np.int32))
+    o = np.array([-1.0, 0.05, 0.02])
+    d = np.array([1.0, 0.1, 0.0])
+    d /= np.linalg.norm(d)
+    t_far = 4.0
+    tstar = np.dot(s2 - s1, 0.5 * (s1 + s2) - o) / np.dot(s2 - s1, d)
+    e1 = math.exp(-sig1 * tstar)
+    e12 = e1 * math.exp(-sig2 * (t_far - tstar))
+    assert 1e-5 < e12 < 0.5 * e1 < 0.5
+
+    def run(T_eps):
+        _, T, k, fl = O.render(sc, o[None], d[None], t_far=t_far, T_eps=T_eps, bg=(1, 1, 1))
+        return T[0], int(k[0]), int(fl[0])
+
+    # next to the T after the first cell: flagged on both sides, and the stop
+    # follows T < T_eps after compositing (one cell above, two below)
+    for rel, steps in ((5e-5, 1), (-5e-5, 2)):
+        T, k, fl = run(e1 * (1 + rel))
+        assert fl & O.F_T_AMBIG and k == steps, (rel, fl, k)
+    # 5e-3 away: not flagged, same stopping rule
+    for rel, steps in ((5e-3, 1), (-5e-3, 2)):
+        T, k, fl = run(e1 * (1 + rel))
+        assert fl == 0 and k == steps, (rel, fl, k)
+        assert abs(T - (e1 if steps == 1 else e12)) < 1e-15
+    # next to the final T (after the second cell): flagged; 5e-3 away: not
+    assert run(e12 * (1 + 5e-5))[2] & O.F_T_AMBIG
+    assert run(e12 * (1 - 5e-5))[2] & O.F_T_AMBIG
+    assert run(e12 * (1 + 5e-3))[2] == 0
+    # next to the T before the first cell (1), which is never a T after a
+    # cell here: not flagged
+    T, k, fl = run(1.0 - 5e-5)
+    assert fl == 0 and k == 1
+
+
 def test_max_steps_flag(tiny):
     wl, sc = tiny
     o, d = W.workload_rays(wl)
