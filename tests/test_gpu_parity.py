@@ -19,6 +19,7 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 import oracle as O  # noqa: E402
+import parity_log  # noqa: E402
 from paper_2608_17682_gb300 import workloads as W  # noqa: E402
 from paper_2608_17682_gb300 import api  # noqa: E402
 
@@ -58,13 +59,29 @@ def fwd_res(scene, to, td, P):
     return rgb, res
 
 
-def compare_sequences(gc, gn, oc, on, flags):
-    """Cell sequences equal for every unflagged ray; returns (#checked, #flagged-mismatch)."""
+def compare_sequences(gc, gn, oc, on, flags, name=None):
+    """Cell sequences equal for every unflagged ray; returns (#checked,
+    #flagged-mismatch). With `name`, the counts go to the run's parity report."""
     ok = (flags & O.BAND_FLAGS) == 0
     same = (gn == on) & np.all(gc == oc, axis=1)
     bad = ok & ~same
+    n_ok, n_band_diff = int(ok.sum()), int((~ok & ~same).sum())
+    if name:
+        parity_log.record(name, rays=len(flags), band=int((~ok).sum()), band_seq_mismatch=n_band_diff,
+                          unflagged_seq_mismatch=int(bad.sum()))
     assert not bad.any(), f"{bad.sum()} unflagged rays differ, first {np.nonzero(bad)[0][:5]}"
-    return int(ok.sum()), int((~ok & ~same).sum())
+    return n_ok, n_band_diff
+
+
+def image_report(name, rgb, orgb, flags):
+    """Image error against the oracle inside and outside the degenerate band
+    (reported; the bars are asserted by the caller)."""
+    ok = (flags & O.BAND_FLAGS) == 0
+    err = np.abs(np.asarray(rgb, np.float64) - orgb)
+    parity_log.record(name, rays=len(flags), band=int((~ok).sum()),
+                      max_err=float(err[ok].max()) if ok.any() else 0.0,
+                      max_err_band=float(err[~ok].max()) if (~ok).any() else 0.0,
+                      rmse=float(np.sqrt(np.mean(err[ok] ** 2))) if ok.any() else 0.0)
 
 
 def grad_close(g, ref, name):
@@ -123,7 +140,8 @@ def test_tiny_forward_parity(tiny, layout):
     oc, ot, on, _ = O.trace(osc, o, d, max_cells=256, params=oracle_params(wl.params))
     ok = (flags & O.BAND_FLAGS) == 0
     assert ok.mean() > 0.95
-    compare_sequences(cells.cpu().numpy(), n_cells.cpu().numpy(), oc, on, flags)
+    compare_sequences(cells.cpu().numpy(), n_cells.cpu().numpy(), oc, on, flags, name=f"tiny forward ({layout})")
+    image_report(f"tiny forward image ({layout})", rgb.cpu().numpy(), orgb, flags)
     assert np.array_equal(steps.cpu().numpy()[ok], osteps[ok])
     assert np.abs(rgb.cpu().numpy()[ok] - orgb[ok]).max() <= IMG_TOL
     assert np.abs(T.cpu().numpy()[ok] - oT[ok]).max() <= IMG_TOL
@@ -143,7 +161,9 @@ def test_medium_forward_parity_ragged_tiles(medium):
     assert scene.get_error()[0] == 0
     orgb, oT, osteps, flags = O.render(osc, o, d, params=oracle_params(base))
     oc, _, on, _ = O.trace(osc, o, d, max_cells=400, params=oracle_params(base))
-    n_ok, n_flag_diff = compare_sequences(cells.cpu().numpy(), n_cells.cpu().numpy(), oc, on, flags)
+    n_ok, n_flag_diff = compare_sequences(cells.cpu().numpy(), n_cells.cpu().numpy(), oc, on, flags,
+                                          name="50k-site forward, ragged tiles")
+    image_report("50k-site forward image", rgb.cpu().numpy(), orgb, flags)
     ok = (flags & O.BAND_FLAGS) == 0
     assert n_ok > 0.95 * len(o)
     assert np.abs(rgb.cpu().numpy()[ok] - orgb[ok]).max() <= IMG_TOL
@@ -163,9 +183,11 @@ def test_half_precision_textures(medium, dtype):
     osq = O.OracleScene(sc.sites, sc.sigma, tq, sc.offsets, sc.indices)
     orgb_q, _, _, flags = O.render(osq, o, d, params=oracle_params(base))
     ok = (flags & O.BAND_FLAGS) == 0
+    image_report(f"50k-site {dtype} textures vs dequantised", rgb, orgb_q, flags)
     assert np.abs(rgb[ok] - orgb_q[ok]).max() <= IMG_TOL
     # (i) oracle on the FP32 textures: total error, RMSE <= 2e-3
     orgb, _, _, _ = O.render(osc, o, d, params=oracle_params(base))
+    image_report(f"50k-site {dtype} textures vs FP32 textures", rgb, orgb, flags)
     rmse = math.sqrt(np.mean((rgb[ok] - orgb[ok]) ** 2))
     assert rmse <= 2e-3, rmse
 
@@ -433,7 +455,8 @@ def test_wide_angle_moving_origin_rays(medium):
     osq = O.OracleScene(sc.sites, sc.sigma, tq, sc.offsets, sc.indices)
     orgb, _, osteps, flags = O.render(osq, o, d, params=oracle_params(base))
     oc, _, on, _ = O.trace(osq, o, d, max_cells=400, params=oracle_params(base))
-    compare_sequences(cells.cpu().numpy(), n_cells.cpu().numpy(), oc, on, flags)
+    compare_sequences(cells.cpu().numpy(), n_cells.cpu().numpy(), oc, on, flags, name="wide-angle moving origins")
+    image_report("wide-angle moving origins image", rgb.cpu().numpy(), orgb, flags)
     ok = (flags & O.BAND_FLAGS) == 0
     assert np.abs(rgb.cpu().numpy()[ok] - orgb[ok]).max() <= IMG_TOL
     assert np.array_equal(steps.cpu().numpy()[ok], osteps[ok])
@@ -497,6 +520,103 @@ def test_mixed_cameras_one_launch(medium):
     lens = a[0][3 * n_px:7 * n_px]
     px = api.average_samples(lens.contiguous(), 4)
     assert torch.allclose(px, lens.view(n_px, 4, 3).mean(1), atol=1e-6)
+
+
+def mixed_camera_rays(cams):
+    """FP32 rays of each camera from the oracle's ray generation (its own
+    pins fix it; the GPU's ray generation is compared with it separately), so
+    that both sides walk the same input rays."""
+    os_, ds = [], []
+    for c in cams:
+        o, d, _ = O.raygen(c)
+        os_.append(o.astype(np.float32))
+        ds.append(d.astype(np.float32))
+    return np.concatenate(os_), np.concatenate(ds)
+
+
+def mixed_launch_against_oracle(name, sc, cams, sel_px, seed, tex_dtype="f16"):
+    """The launch path of the mixed-camera workload against the oracle: all
+    cameras' rays in one image-table launch (one anchor per image; thin-lens,
+    rolling-shutter and motion-blur origins reach their start cells by
+    descent from the anchor), lens/time samples averaged per pixel by
+    vt_average_samples, and the backward through vt_average_samples_bwd.
+    `sel_px[k]` are the pixels of camera k the oracle computes: cells (exact
+    outside the band), colours, pixel averages, gradients."""
+    o, d = mixed_camera_rays(cams)
+    sizes = [(c.w * c.spp, c.h) for c in cams]
+    base = W.default_params()
+    P = gpu_params(base, image_sizes=sizes)
+    scene = api.Scene.from_workload(sc, tex_dtype=tex_dtype)
+    to, td = to_dev(o, d)
+    res = torch.empty(len(o), 3, device=DEV)
+    rgb, T, steps = api.render_fwd(scene, to, td, P, residual=res)
+    assert scene.get_error()[0] == 0
+    # the sampled rays: every lens / time sample of each selected pixel
+    first = np.cumsum([0] + [c.n_rays for c in cams])
+    sel = np.concatenate([first[k] + (np.asarray(px)[:, None] * c.spp + np.arange(c.spp)[None]).ravel()
+                          for k, (c, px) in enumerate(zip(cams, sel_px))])
+    tq = sc.tex if tex_dtype == "f32" else torch.as_tensor(sc.tex).half().float().numpy()
+    osq = O.OracleScene(sc.sites, sc.sigma, tq, sc.offsets, sc.indices)
+    op = oracle_params(base)
+    orgb, oT, osteps, flags = O.render(osq, o[sel], d[sel], params=op)
+    ok = (flags & O.BAND_FLAGS) == 0
+    assert ok.mean() > 0.95
+    g_rgb = rgb.cpu().numpy()[sel]
+    image_report(name + " image", g_rgb, orgb, flags)
+    assert np.abs(g_rgb[ok] - orgb[ok]).max() <= IMG_TOL
+    assert np.abs(T.cpu().numpy()[sel][ok] - oT[ok]).max() <= IMG_TOL
+    assert np.array_equal(steps.cpu().numpy()[sel][ok], osteps[ok])
+    cells, _, n_cells = api.trace_cells(scene, to[sel].contiguous(), td[sel].contiguous(), gpu_params(base),
+                                        max_cells=512)
+    oc, _, on, _ = O.trace(osq, o[sel], d[sel], max_cells=512, params=op)
+    compare_sequences(cells.cpu().numpy(), n_cells.cpu().numpy(), oc, on, flags, name=name)
+    # pixel averages of the multi-sample cameras; a pixel is checked when all
+    # its samples are outside the band
+    rng = np.random.default_rng(seed)
+    g_px_all, g_ray_o = [], np.zeros((len(sel), 3))
+    pos = 0
+    for k, (c, px) in enumerate(zip(cams, sel_px)):
+        m = len(px) * c.spp
+        ok_px = ok[pos:pos + m].reshape(len(px), c.spp).all(1)
+        g_px = np.zeros((c.n_rays // c.spp, 3), np.float32)
+        g_px[np.asarray(px)[ok_px]] = rng.normal(size=(ok_px.sum(), 3))
+        if c.spp > 1:
+            blk = rgb[first[k]:first[k + 1]].contiguous()
+            avg = api.average_samples(blk, c.spp).cpu().numpy()[np.asarray(px)]
+            o_avg = orgb[pos:pos + m].reshape(len(px), c.spp, 3).mean(1)
+            assert np.abs(avg[ok_px] - o_avg[ok_px]).max() <= IMG_TOL
+        # dL/d(sample colour) = dL/d(pixel) / spp: the adjoint of the mean
+        g_ray_o[pos:pos + m] = np.repeat(g_px[np.asarray(px)].astype(np.float64), c.spp, axis=0) / c.spp
+        g_px_all.append(torch.as_tensor(g_px, device=DEV))
+        pos += m
+    g_dev = torch.cat([api.average_samples_bwd(gp, c.spp) if c.spp > 1 else gp
+                       for gp, c in zip(g_px_all, cams)]).contiguous()
+    gs, gsig, gt = api.render_bwd(scene, to, td, P, rgb, g_dev, residual=res)
+    assert scene.get_error()[0] == 0
+    ogs, ogsig, ogt = O.render_bwd(osq, o[sel], d[sel], g_ray_o, params=op)
+    grad_close(gsig.cpu().numpy(), ogsig, name + " sigma")
+    grad_close(gs.cpu().numpy(), ogs, name + " sites")
+    gt = gt.cpu().numpy()
+    touched = np.nonzero(np.abs(ogt).reshape(len(ogt), -1).max(1) > 0)[0]
+    grad_close(gt[touched], ogt[touched], name + " tex")
+    rest = np.setdiff1d(np.arange(len(ogt)), touched)
+    assert np.abs(gt.reshape(len(ogt), -1)[rest]).max() == 0
+
+
+def test_mixed_cameras_image_table_against_oracle(medium):
+    """Pinhole, equidistant fisheye, rolling shutter, thin lens (4 lens
+    samples) and motion blur (2 time samples) in one image-table launch on the
+    50k-site scene, every ray against the oracle."""
+    sc, osc, o_, d_, cams_ = medium
+    o0 = np.zeros(3)
+    cams = [W.look_at_camera(0, 48, 32, W.orbit_eye(o0, 3.0, 10, 20), o0),
+            W.look_at_camera(1, 48, 32, W.orbit_eye(o0, 3.0, 100, 20), o0, fisheye_fov=math.pi),
+            W.look_at_camera(2, 48, 32, W.orbit_eye(o0, 3.0, 190, 20), o0, rs_velocity=(0.05, 0.0, 0.0)),
+            W.look_at_camera(3, 48, 32, W.orbit_eye(o0, 3.0, 280, 20), o0, lens_radius=0.01, focus_dist=3.0,
+                             lens_samples=4, seed=7),
+            W.look_at_camera(4, 48, 32, W.orbit_eye(o0, 3.0, 330, 20), o0, rs_velocity=(0.0, 0.02, 0.01),
+                             lens_samples=2, seed=8)]
+    mixed_launch_against_oracle("50k-site mixed cameras", sc, cams, [np.arange(48 * 32)] * len(cams), seed=91)
 
 
 def test_keep_order_scene_gives_identical_results(medium):

@@ -1,14 +1,16 @@
 """Full-size parity at the benchmark's scale and launch configuration:
 3,000,000 surface-concentrated sites, 8x8 textures, four 1280x832 views
-(4,259,840 rays in one launch, image layout, 4x8 tiles), FP32 and FP16
-texture storage, and the paper's appearance model with the distortion loss. The oracle computes a strided sample of the rays one by one
-(every 997th ray); gradients are compared for a launch over all rays in which
-only the sampled rays carry dL/dC. Ray generation of the 16 mixed cameras
-(pinhole, fisheye, rolling shutter, thin lens: 29,818,880 rays) is compared
+(4,259,840 rays in one launch, image layout, 4x8 tiles) with FP32, FP16 and
+BF16 texture storage, and the paper's appearance model with the distortion
+loss; the mixed-camera workload (16 cameras, 29,818,880 rays in one
+image-table launch). The oracle computes a strided sample of the rays one by
+one (every 997th ray of the four views, every 4001st pixel of the mixed
+cameras); gradients are compared for a launch over all rays in which only the
+sampled rays carry dL/dC. Ray generation of the 16 mixed cameras is compared
 with the oracle's ray generation camera by camera.
 
-The 3M-site Delaunay triangulation takes a few minutes on the host the first
-time; it is cached on local disk for the benchmark.
+The 3M-site Delaunay triangulations take a few minutes on the host the first
+time; they are cached on local disk for the benchmark.
 """
 import math
 
@@ -25,7 +27,7 @@ import oracle as O  # noqa: E402
 from paper_2608_17682_gb300 import api  # noqa: E402
 from paper_2608_17682_gb300 import workloads as W  # noqa: E402
 
-from test_gpu_parity import compare_sequences, grad_close, IMG_TOL  # noqa: E402
+from test_gpu_parity import compare_sequences, grad_close, image_report, IMG_TOL, mixed_launch_against_oracle  # noqa: E402,E501
 
 STRIDE = 997
 
@@ -38,7 +40,7 @@ def big():
     return wl, o, d, sel
 
 
-@pytest.mark.parametrize("dtype", ["f32", "f16"])
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
 def test_fullsize_forward_and_backward(big, dtype):
     wl, o, d, sel = big
     sc = wl.scene
@@ -50,24 +52,27 @@ def test_fullsize_forward_and_backward(big, dtype):
     res = torch.empty(len(o), 3, device="cuda")
     rgb, T, steps = api.render_fwd(scene, to, td, P, residual=res)
     assert scene.get_error()[0] == 0
-    tex = sc.tex if dtype == "f32" else torch.as_tensor(sc.tex).half().float().numpy()
+    q = {"f16": torch.float16, "bf16": torch.bfloat16}
+    tex = sc.tex if dtype == "f32" else torch.as_tensor(sc.tex).to(q[dtype]).float().numpy()
     osc = O.OracleScene(sc.sites, sc.sigma, tex, sc.offsets, sc.indices)
     op = O.make_params(**wl.params)
     orgb, oT, osteps, flags = O.render(osc, o[sel], d[sel], params=op)
     ok = (flags & O.BAND_FLAGS) == 0
     assert ok.mean() > 0.95
     g_rgb = rgb.cpu().numpy()[sel]
+    image_report(f"3M-site {dtype} textures (oracle on the stored texels)", g_rgb, orgb, flags)
     assert np.abs(g_rgb[ok] - orgb[ok]).max() <= IMG_TOL
     assert np.array_equal(steps.cpu().numpy()[sel][ok], osteps[ok])
     # cell sequences of the sampled rays
     cells, _, n_cells = api.trace_cells(scene, to[sel].contiguous(), td[sel].contiguous(), api.make_params(**wl.params),
                                         max_cells=512)
     oc, _, on, _ = O.trace(osc, o[sel], d[sel], max_cells=512, params=op)
-    compare_sequences(cells.cpu().numpy(), n_cells.cpu().numpy(), oc, on, flags)
-    if dtype == "f16":
+    compare_sequences(cells.cpu().numpy(), n_cells.cpu().numpy(), oc, on, flags, name=f"3M-site {dtype} textures")
+    if dtype != "f32":
         # total error against the FP64 oracle on the FP32 textures
         o32 = O.OracleScene.from_workload_scene(sc)
         orgb32 = O.render(o32, o[sel], d[sel], params=op)[0]
+        image_report(f"3M-site {dtype} textures vs FP32 textures", g_rgb, orgb32, flags)
         rmse = math.sqrt(np.mean((g_rgb[ok] - orgb32[ok]) ** 2))
         assert rmse <= 2e-3, rmse
     # backward over all rays; only sampled, unflagged rays carry a gradient
@@ -146,3 +151,14 @@ def test_fullsize_mixed_camera_raygen():
         assert np.abs(gd - od).max() <= 4e-6, c.kind
         assert np.abs(gt - ot).max() <= 1e-7, c.kind
         base += n
+
+
+def test_fullsize_mixed_cameras_against_oracle():
+    """The mixed-camera workload as the benchmark launches it: 3,000,000 sites
+    (FP16 8x8 textures), 4 pinhole, 4 fisheye, 4 rolling-shutter and 4
+    thin-lens (4 lens samples) cameras of 1280x832, 29,818,880 rays in one
+    image-table launch, forward and backward. Every 4001st pixel of each
+    camera (all its lens samples) against the oracle."""
+    wl = W.make_workload("mixed3m")
+    sel_px = [np.arange(0, c.n_rays // c.spp, 4001) for c in wl.cameras]
+    mixed_launch_against_oracle("3M-site mixed cameras", wl.scene, wl.cameras, sel_px, seed=13)

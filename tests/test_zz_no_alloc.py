@@ -62,6 +62,30 @@ def test_static_backward_matches_allocating_backward_twice():
             _close(a, b, f"call {call} {name}")
 
 
+def test_static_backward_matches_the_oracle():
+    """The same entry point against the FP64 oracle directly, on the rays
+    outside the degenerate band (the others carry no gradient)."""
+    import oracle as O
+
+    wl = W.make_workload("tiny")
+    o, d = W.workload_rays(wl)
+    osc = O.OracleScene.from_workload_scene(wl.scene)
+    op = O.make_params(**wl.params)
+    flags = O.render(osc, o, d, params=op)[3]
+    ok = (flags & O.BAND_FLAGS) == 0
+    g = (np.random.default_rng(7).normal(size=(len(o), 3)) * ok[:, None]).astype(np.float32)
+    P = api.make_params(**wl.params, img_w=64, img_h=64, n_images=1)
+    scene = api.Scene.from_workload(wl.scene)
+    to = torch.as_tensor(o, device="cuda")
+    td = torch.as_tensor(d, device="cuda")
+    rgb = api.render_fwd(scene, to, td, P)[0]
+    got = _static_bwd(scene, to, td, P, rgb, torch.as_tensor(g, device="cuda"))
+    assert scene.get_error()[0] == 0
+    ref = O.render_bwd(osc, o, d, g.astype(np.float64), params=op)
+    for name, a, b in zip(("sites", "sigma", "tex"), got, ref):
+        _close(a, torch.as_tensor(b), f"oracle {name}")
+
+
 def test_static_backward_rejects_scene_beyond_capacity():
     # 40,000 sites with 8x8 textures need 40,000 * 65 * 16 bytes > 32 MiB
     sc = W.make_scene("uniform", 40_000, 8, 31)
@@ -71,6 +95,14 @@ def test_static_backward_rejects_scene_beyond_capacity():
     P = api.make_params()
     rgb = api.render_fwd(scene, o, d, P)[0]
     g = torch.ones(4, 3, device="cuda")
+    gs = torch.full((scene.n, 3), float("nan"), device="cuda")
+    gsig = torch.full((scene.n,), float("nan"), device="cuda")
+    gt = torch.full((scene.n, scene.R, scene.R, 3), float("nan"), device="cuda")
     with pytest.raises(_vt.VTError) as e:
-        _static_bwd(scene, o, d, P, rgb, g)
+        _vt.vt_render_bwd_static(scene.handle, o.shape[0], o.data_ptr(), d.data_ptr(), 0, P, rgb.data_ptr(),
+                                 g.data_ptr(), gs.data_ptr(), gsig.data_ptr(), gt.data_ptr(),
+                                 torch.cuda.current_stream().cuda_stream)
     assert e.value.status == _vt.VT_ERR_CAPACITY
+    # a rejected call writes nothing
+    torch.cuda.synchronize()
+    assert torch.isnan(gs).all() and torch.isnan(gsig).all() and torch.isnan(gt).all()
