@@ -210,12 +210,66 @@ def recorded_traffic(kernel, workload):
     return None
 
 
+def recorded_issue(kernel, workload):
+    """Issue-slot activity (fraction of cycles a warp instruction issued) of
+    the kernel from the committed ncu summaries (lines "ISSUE <kernel>
+    <workload> <fraction> <source hash>"), on the current sources only."""
+    d = os.path.join(ROOT, "profiles")
+    try:
+        names = sorted(os.listdir(d))
+    except OSError:
+        return None
+    h = kernel_source_hash()
+    for n in names:
+        if not n.endswith(".md"):
+            continue
+        with open(os.path.join(d, n)) as f:
+            for line in f:
+                w = line.split()
+                if len(w) == 5 and w[0] == "ISSUE" and w[1] == kernel and w[2] == workload and w[4] == h:
+                    return float(w[3])
+    return None
+
+
+def l2_bandwidth(torch, dev, stream):
+    """L2 read bandwidth: vt_stream_read over buffers that fit in the 129 MB
+    L2, repeated in one kernel, CUDA events; the best over the sizes. Also the
+    same probe over a 4 GB buffer (HBM read bandwidth) for context."""
+    from paper_2608_17682_gb300 import _vt
+
+    sink = torch.zeros(1, device=dev)
+    out = {}
+    best = 0.0
+    for mb in (24, 48, 96):
+        buf = torch.ones(mb * (1 << 20) // 4, device=dev)
+        reps = max(4, int(64e9 // buf.numel() // 4 // 4))  # about 16 GB read per timing
+        _vt.vt_stream_read(buf.data_ptr(), buf.numel() * 4, 2, sink.data_ptr(), stream.cuda_stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _vt.vt_stream_read(buf.data_ptr(), buf.numel() * 4, reps, sink.data_ptr(), stream.cuda_stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        gbs = buf.numel() * 4 * reps / (a.elapsed_time(b) * 1e-3) / 1e9
+        out[f"{mb}MB"] = round(gbs, 1)
+        best = max(best, gbs)
+        del buf
+    big = torch.ones((4 << 30) // 4, device=dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    _vt.vt_stream_read(big.data_ptr(), big.numel() * 4, 3, sink.data_ptr(), stream.cuda_stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    hbm = big.numel() * 4 * 3 / (a.elapsed_time(b) * 1e-3) / 1e9
+    del big
+    return {"l2_read_gbs": round(best, 1), "by_buffer": out, "hbm_read_gbs_4GB": round(hbm, 1)}
+
+
 # ---------------------------------------------------------------- our arm
 
 def run_ours(args, ws, rank, local):
     import torch
 
-    from paper_2608_17682_gb300 import api
+    from paper_2608_17682_gb300 import _vt, api
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -335,8 +389,13 @@ def run_ours(args, ws, rank, local):
     clocks = ClockSampler(local)
     clocks.start()
     walks = {}
+    launches0 = _vt.vt_kernel_launches()
     ms_step, ms_fwd, ms_bwd = timed(main, args.steps, walks=walks)
+    # the library's own kernel launches per step, counted by the library
+    # (warm-up and timed steps are identical)
+    launches_per_step = (_vt.vt_kernel_launches() - launches0) / (args.warmup + args.steps)
     clk = clocks.stop()
+    grads_main = [x.clone() for x in (gs, gsig, gt)] if not args.no_extra else None
     # the max over ranks
     if ws > 1:
         t = torch.tensor([ms_step], device=dev)
@@ -353,10 +412,57 @@ def run_ours(args, ws, rank, local):
     extra = {}
     ms_f, fwd_only_fwd, _ = timed(main, max(3, args.steps // 2), fwd_only=True)
     extra["fwd_only_mrays_s"] = round(n_rays / (ms_f * 1e-3) / 1e6 * ws, 2)
+    grads_by_dtype = {args.tex: grads_main}
     for t in dtypes[1:]:
-        m_s, m_f, m_b = timed(scenes[t], max(3, args.steps // 2))
+        w_t = {}
+        m_s, m_f, m_b = timed(scenes[t], max(3, args.steps // 2), walks=w_t)
         extra[t] = {"fwd_bwd_mrays_s": round(n_rays / (m_s * 1e-3) / 1e6 * ws, 2), "ms_fwd": round(m_f, 3),
-                    "ms_bwd": round(m_b, 3)}
+                    "ms_bwd": round(m_b, 3), "ms_walk_kernel": {"fwd": round(w_t["fwd"], 4),
+                                                                "bwd": round(w_t["bwd"], 4)}}
+        grads_by_dtype[t] = [x.clone() for x in (gs, gsig, gt)]
+    # gradients of the same L2 step with each texture storage against the FP32 kernel's
+    if "f32" in grads_by_dtype and grads_by_dtype["f32"] is not None:
+        ref = grads_by_dtype["f32"]
+        for t, gg in grads_by_dtype.items():
+            if t == "f32" or gg is None:
+                continue
+            extra.setdefault(t, {})["grad_vs_f32_kernel"] = {
+                name: round(((a.double() - b.double()).norm() / b.double().norm()).item(), 6)
+                for name, a, b in zip(("sites", "sigma", "tex"), gg, ref)}
+    del grads_by_dtype, grads_main
+
+    # region 3 of the timing protocol: the torch.autograd.Function path
+    # (VTRender.apply, an L2 loss in torch ops, loss.backward())
+    if not args.appearance:
+        sites_t = torch.tensor(wl.scene.sites, device=dev, requires_grad=True)
+        sigma_t = torch.tensor(wl.scene.sigma, device=dev, requires_grad=True)
+        tex_t = torch.tensor(wl.scene.tex, device=dev, requires_grad=True)
+
+        def autograd_step():
+            for p_ in (sites_t, sigma_t, tex_t):
+                p_.grad = None
+            api.generate_rays(cams, out=(o, d, tm))
+            img = api.render(sites_t, sigma_t, tex_t, o, d, main, params)
+            loss_ = ((img - Y) ** 2).mean()
+            loss_.backward()
+
+        for _ in range(args.warmup):
+            autograd_step()
+        barrier()
+        reps, tot = max(3, args.steps // 2), 0.0
+        for _ in range(reps):
+            flush.zero_()
+            a, b = ev(), ev()
+            a.record(stream)
+            autograd_step()
+            b.record(stream)
+            barrier()
+            tot += a.elapsed_time(b)
+        extra["autograd_region"] = {"fwd_bwd_mrays_s": round(n_rays / (tot / reps * 1e-3) / 1e6 * ws, 2),
+                                    "ms_per_step": round(tot / reps, 3),
+                                    "what": "VTRender.apply + torch L2 loss + loss.backward(), ray generation "
+                                            "included, L2 flushed between steps"}
+        del sites_t, sigma_t, tex_t
     if not args.no_extra:
         # the other appearance model as a comparison line
         other = 1 - args.appearance
@@ -524,25 +630,41 @@ def run_ours(args, ws, rank, local):
     e2e = {"value": round(total_rays / (ms_e2e * 1e-3) / 1e6, 3), "unit": "Mrays/s",
            "h2d_bytes_per_step": int(Yh.numel() * 4), "d2h_bytes_per_step": int(rgb_h.numel() * 4 + 4)}
 
-    # roofline of the dominant kernel (algorithmic bytes per visited cell)
+    # roofline of the dominant kernel: algorithmic (demand) bytes per visited
+    # cell, the byte model of the scope table: cell record, neighbour records,
+    # texels; the backward adds the gradient operands sent to the L2 atomics
+    # (sigma 4 B, both sites of the crossed face 24 B, 4 texels x 3 channels
+    # 48 B per map)
     peaks, peak_kind = measured_peaks()
     E = main.n_edges
     tb = 8 if args.tex in ("f16", "bf16") else 16
-    n_tex = 8 if args.appearance else 4  # texels read per coloured cell (two maps for the paper's model)
-    b_fwd_step = 32 + 16 * E / N + n_tex * tb  # cell record + neighbour plane records + texels
-    b_bwd_step = b_fwd_step + 2 * (16 + n_tex * 16)  # + RMW of one cell and the texel gradient float4s
+    n_maps = 2 if args.appearance else 1  # texture maps read per coloured cell
+    b_fwd_step = 32 + 16 * E / N + 4 * n_maps * tb
+    b_bwd_step = b_fwd_step + 4 + 24 + 48 * n_maps
     io_fwd, io_bwd = 24 + 20, 24 + 24
     dom = "bwd" if walks["bwd"] >= walks["fwd"] else "fwd"
     ms_dom = walks[dom]  # the walk kernel alone (library-recorded events)
     alg = sum_steps * (b_bwd_step if dom == "bwd" else b_fwd_step) + n_rays * (io_bwd if dom == "bwd" else io_fwd)
     achieved = alg / (ms_dom * 1e-3) / 1e9
-    peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+    hbm_peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+    l2 = l2_bandwidth(torch, dev, stream)
     # the walk instantiation: mode, texel storage, appearance model
     kname = f"k_walk<{dom.upper()},{args.tex}" + (",appearance1>" if args.appearance else ">")
-    roof = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": recorded_traffic(kname, args.workload),
-            "algorithmic_bytes_per_launch": int(alg), "peak_source": f"{peak_kind} hbm_gbs",
-            "ms_per_launch": round(ms_dom, 4)}
+    traffic = recorded_traffic(kname, args.workload)
+    issue = recorded_issue(kname, args.workload)
+    # achieved = demand bytes / event-timed kernel; frac against the measured
+    # HBM copy peak; the same demand against the L2 read bandwidth measured
+    # here; DRAM bytes (ncu) / kernel time against the HBM peak. The kernel is
+    # bound by instruction issue (ncu), not by either bandwidth.
+    roof = {"bound": "issue", "kernel": kname, "achieved": round(achieved, 1), "peak": hbm_peak,
+            "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
+            "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": int(alg),
+            "bytes_per_step": {"fwd": round(b_fwd_step, 1), "bwd": round(b_bwd_step, 1)},
+            "ms_per_launch": round(ms_dom, 4),
+            "l2_read_gbs": l2["l2_read_gbs"], "demand_vs_l2_frac": round(achieved / l2["l2_read_gbs"], 4),
+            "dram_gbs": None if traffic is None else round(traffic / (ms_dom * 1e-3) / 1e9, 1),
+            "dram_frac": None if traffic is None else round(traffic / (ms_dom * 1e-3) / 1e9 / hbm_peak, 4),
+            "issue_active_ncu": issue, "probe": l2}
 
     line = {
         "metric": metric_name(args),
@@ -558,10 +680,12 @@ def run_ours(args, ws, rank, local):
         "ms_walk_kernel": {"fwd": round(walks["fwd"], 4), "bwd": round(walks["bwd"], 4)},
         "fps_fwd_bwd": round(n_img / (ms_step * 1e-3), 2),
         "mean_cells_per_ray": round(sum_steps / n_rays, 3), "fp64_rechecks_per_step": fp64 / max(1, args.steps + args.warmup),
-        "clocks": clk, "e2e": e2e, "gpu_launches": 9 * args.steps, "roofline": roof, **extra,
+        "clocks": clk, "e2e": e2e, "gpu_launches": int(round(launches_per_step * args.steps)),
+        "gpu_launches_per_step": launches_per_step, "roofline": roof, **extra,
     }
     if rank == 0 and ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args, wl, cams, args.cpu_seconds)
+        line["accuracy"] = accuracy_vs_oracle(args, wl, cams, scenes, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -614,6 +738,81 @@ def cpu_baseline(args, wl, cams, seconds):
     return {"value": round(rate, 6), "unit": "Mrays/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"{len(o)} rays strided over the views, fwd (threaded) + bwd (threaded walk, serial "
                       f"accumulation), FP64, {dt:.1f} s"}
+
+
+def accuracy_vs_oracle(args, wl, cams, scenes, dev, n=4096):
+    """Error of the timed kernels against the FP64 oracle (the oracle leg of
+    the benchmark, outside every timed region), per texture storage type, on
+    a fixed strided sample of the benchmark's rays (generated by the oracle's
+    ray generation, FP32, rendered by both sides in one 1-D launch):
+      image RMSE / max abs vs the oracle on the FP32 textures (total error)
+      and on the dequantised textures (kernel error), over the rays outside
+      the degenerate band; band-flagged rays and how many of them follow
+      another cell sequence; gradient error of a backward in which only the
+      sample's unflagged rays carry dL/dC (seeded normal), worst entry of
+      |g - g_ref| / max(|g_ref|, 1e-3 max|g_ref|) against the oracle on the
+      stored (dequantised) textures."""
+    import torch
+
+    import oracle as O
+    from paper_2608_17682_gb300 import api
+
+    o, d = oracle_sample_rays(cams, n)
+    osc32, op = oracle_setup(args, wl)
+    orgb32, oT, osteps, flags = O.render(osc32, o, d, params=op)
+    ok = (flags & O.BAND_FLAGS) == 0
+    oc, _, on, _ = O.trace(osc32, o, d, max_cells=1024, params=op)
+    g = (np.random.default_rng(17).normal(size=(len(o), 3)) * ok[:, None]).astype(np.float32)
+    to = torch.as_tensor(o, device=dev)
+    td = torch.as_tensor(d, device=dev)
+    tg = torch.as_tensor(g, device=dev)
+    P1 = api.make_params(**wl.params, appearance=args.appearance)
+    out = {"sample": f"{len(o)} rays strided over the views (oracle ray generation), 1-D launch",
+           "rays_outside_band": int(ok.sum()), "band_flagged": int((~ok).sum())}
+    first = next(iter(scenes.values()))
+    cells, _, n_cells = api.trace_cells(first, to, td, P1, max_cells=1024)
+    same = (n_cells.cpu().numpy() == on) & np.all(cells.cpu().numpy() == oc, axis=1)
+    out["band_seq_mismatch"] = int((~ok & ~same).sum())
+    out["unflagged_seq_mismatch"] = int((ok & ~same).sum())
+
+    def img_err(a, b):
+        e = np.abs(a[ok].astype(np.float64) - b[ok])
+        return {"rmse": float(f"{math.sqrt(np.mean(e ** 2)):.3g}"), "max_abs": float(f"{e.max():.3g}")}
+
+    def grad_err(a, b):
+        a = a.cpu().numpy().astype(np.float64)
+        floor = 1e-3 * np.abs(b).max()
+        return float(f"{(np.abs(a - b) / np.maximum(np.abs(b), floor)).max():.3g}") if floor > 0 else 0.0
+
+    qt = {"f16": torch.float16, "bf16": torch.bfloat16}
+    for t, scene in scenes.items():
+        res = torch.empty(len(o), 3, device=dev)
+        rgb, _, steps = api.render_fwd(scene, to, td, P1, residual=res)
+        if t == "f32":
+            osq, orgb_q = osc32, orgb32
+        else:
+            q = lambda x: torch.as_tensor(x).to(qt[t]).float().numpy()  # noqa: E731
+            sc = wl.scene
+            if args.appearance:
+                tvi, tvd = appearance_maps(wl)
+                osq = O.OracleScene(sc.sites, sc.sigma, q(tvi), sc.offsets, sc.indices, tex_vd=q(tvd))
+            else:
+                osq = O.OracleScene(sc.sites, sc.sigma, q(sc.tex), sc.offsets, sc.indices)
+            orgb_q = O.render(osq, o, d, params=op)[0]
+        rgb_h = rgb.cpu().numpy()
+        entry = {"image_vs_oracle_fp32_tex": img_err(rgb_h, orgb32),
+                 "image_vs_oracle_stored_tex": img_err(rgb_h, orgb_q),
+                 "steps_equal_outside_band": bool(np.array_equal(steps.cpu().numpy()[ok], osteps[ok]))}
+        gvd = torch.empty(wl.scene.n, wl.scene.R, wl.scene.R, 3, device=dev) if args.appearance else None
+        gs_, gsig_, gt_ = api.render_bwd(scene, to, td, P1, rgb, tg, residual=res, tex_vd_out=gvd)
+        ref = O.render_bwd(osq, o, d, g.astype(np.float64), params=op)
+        entry["grad_rel_err_vs_oracle"] = {"sites": grad_err(gs_, ref[0]), "sigma": grad_err(gsig_, ref[1]),
+                                           "tex": grad_err(gt_, ref[2])}
+        if args.appearance:
+            entry["grad_rel_err_vs_oracle"]["tex_vd"] = grad_err(gvd, ref[3])
+        out[t] = entry
+        del ref, osq, gs_, gsig_, gt_, gvd
+    return out
 
 
 def run_reference(args, ws, rank):

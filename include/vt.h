@@ -365,6 +365,22 @@ vt_status vt_texture_regularizers(int64_t n_cells, int32_t tex_res, const float*
 vt_status vt_adam_step(int64_t n, float* param, const float* grad, float* m, float* v, float lr, float beta1,
                        float beta2, float eps, int64_t step, void* stream);
 
+/* ---- measurement aids (no counterpart in the paper) */
+
+/* Number of kernels this library has launched in the process so far (all
+ * devices and threads). A caller takes the difference around a region to
+ * count the library's launches in it. */
+uint64_t vt_kernel_launches(void);
+
+/* Bandwidth probe: read the DEVICE buffer `buf` (16-byte aligned, `bytes` a
+ * multiple of 16) `reps` times in one kernel, through the L2 only (the loads
+ * bypass L1). With a buffer that fits in L2 and many repetitions, bytes*reps
+ * over the kernel's time is the L2 read bandwidth; with a buffer larger than
+ * L2 it is the HBM read bandwidth. `sink` is one DEVICE float that is written
+ * only on a value the data never produces. VT_ERR_INVALID_ARG on a bad
+ * pointer, size or count. */
+vt_status vt_stream_read(const void* buf, int64_t bytes, int32_t reps, float* sink, void* stream);
+
 /* Human-readable status name (static string). */
 const char* vt_status_str(vt_status s);
 

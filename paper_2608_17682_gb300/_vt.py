@@ -23,7 +23,7 @@ EXPORTS = ["vt_render_params_default", "vt_scene_create", "vt_scene_update", "vt
            "vt_scene_get_error", "vt_camera_n_rays", "vt_generate_rays", "vt_render_fwd", "vt_render_bwd",
            "vt_render_bwd_static", "vt_trace_cells", "vt_l2_loss", "vt_average_samples", "vt_average_samples_bwd", "vt_sigma_from_rho",
            "vt_sigma_from_rho_bwd", "vt_sample_rays", "vt_smooth_l1_loss", "vt_texture_regularizers", "vt_adam_step",
-           "vt_status_str"]
+           "vt_kernel_launches", "vt_stream_read", "vt_status_str"]
 
 
 class VTError(RuntimeError):
@@ -85,6 +85,8 @@ def _load():
         "vt_smooth_l1_loss": ([I64, P, P, C.c_float, P, P, P], C.c_int),
         "vt_texture_regularizers": ([I64, I32, P, P, C.c_float, C.c_float, P, P, P, P], C.c_int),
         "vt_adam_step": ([I64, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, I64, P], C.c_int),
+        "vt_kernel_launches": ([], C.c_uint64),
+        "vt_stream_read": ([P, I64, I32, P, P], C.c_int),
         "vt_status_str": ([C.c_int], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -233,3 +235,12 @@ def vt_adam_step(n: int, param: int, grad: int, m: int, v: int, lr: float, beta1
                  step: int, stream: int):
     check(lib.vt_adam_step(n, C.c_void_p(param), C.c_void_p(grad), C.c_void_p(m), C.c_void_p(v), lr, beta1, beta2,
                            eps, step, C.c_void_p(stream)), "vt_adam_step")
+
+
+def vt_kernel_launches() -> int:
+    """Kernels the library has launched in this process so far."""
+    return int(lib.vt_kernel_launches())
+
+
+def vt_stream_read(buf: int, nbytes: int, reps: int, sink: int, stream: int):
+    check(lib.vt_stream_read(C.c_void_p(buf), nbytes, reps, C.c_void_p(sink), C.c_void_p(stream)), "vt_stream_read")

@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "vt.h"
 
 #define VT_MAX_ANCHORS 64
@@ -56,6 +58,11 @@ struct vt_scene {
   uint8_t* g_touched = nullptr;
   bool g_tex_clean = false;
 };
+
+// Kernels this library has launched since the process started (all devices
+// and threads), read with vt_kernel_launches(); every launch site adds one.
+extern std::atomic<unsigned long long> g_vt_launches;
+static inline void vt_note_launch() { g_vt_launches.fetch_add(1, std::memory_order_relaxed); }
 
 static inline size_t vt_texel_bytes(int32_t dtype) { return dtype == VT_F32 ? 16 : 8; }
 

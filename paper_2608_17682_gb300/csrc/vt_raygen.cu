@@ -201,9 +201,11 @@ vt_status vt_generate_rays(const vt_camera* cams, int32_t n_cams, float* o, floa
       acc += vt_camera_n_rays(&cams[c0 + k]);
     }
     B.first[B.n] = acc;
-    if (acc > 0)
+    if (acc > 0) {
+      vt_note_launch();
       k_raygen<<<vt_grid(acc, 256, 152 * 64), 256, 0, st>>>(B, acc, o + 3 * base, d + 3 * base,
                                                             time ? time + base : nullptr);
+    }
     VT_CUDA_TRY(cudaGetLastError());
     base += acc;
   }
@@ -216,6 +218,7 @@ vt_status vt_l2_loss(int64_t n, const float* rgb, const float* target, float* gr
   cudaStream_t st = (cudaStream_t)stream;
   VT_CUDA_TRY(cudaMemsetAsync(loss_out, 0, sizeof(float), st));
   if (n == 0) return VT_OK;
+  vt_note_launch();
   k_l2<<<vt_grid(3 * n, 256, 152 * 8), 256, 0, st>>>(3 * n, 1.0f / (float)(3 * n), rgb, target, grad_out, loss_out);
   VT_CUDA_TRY(cudaGetLastError());
   return VT_OK;
@@ -224,6 +227,7 @@ vt_status vt_l2_loss(int64_t n, const float* rgb, const float* target, float* gr
 vt_status vt_average_samples(int64_t n_pixels, int32_t spp, const float* rgb_rays, float* rgb_px, void* stream) {
   if (n_pixels < 0 || spp < 1 || (n_pixels > 0 && (!rgb_rays || !rgb_px))) return VT_ERR_INVALID_ARG;
   if (n_pixels == 0) return VT_OK;
+  vt_note_launch();
   k_avg<<<vt_grid(3 * n_pixels, 256, 152 * 64), 256, 0, (cudaStream_t)stream>>>(n_pixels, spp, rgb_rays, rgb_px);
   VT_CUDA_TRY(cudaGetLastError());
   return VT_OK;
@@ -233,6 +237,7 @@ vt_status vt_average_samples_bwd(int64_t n_pixels, int32_t spp, const float* gra
                                  void* stream) {
   if (n_pixels < 0 || spp < 1 || (n_pixels > 0 && (!grad_px || !grad_rays))) return VT_ERR_INVALID_ARG;
   if (n_pixels == 0) return VT_OK;
+  vt_note_launch();
   k_avg_bwd<<<vt_grid(3 * n_pixels * spp, 256, 152 * 64), 256, 0, (cudaStream_t)stream>>>(n_pixels, spp, grad_px,
                                                                                            grad_rays);
   VT_CUDA_TRY(cudaGetLastError());
@@ -242,6 +247,7 @@ vt_status vt_average_samples_bwd(int64_t n_pixels, int32_t spp, const float* gra
 vt_status vt_sigma_from_rho(int64_t n, const float* rho, float* sigma, void* stream) {
   if (n < 0 || (n > 0 && (!rho || !sigma))) return VT_ERR_INVALID_ARG;
   if (n == 0) return VT_OK;
+  vt_note_launch();
   k_exp<<<vt_grid(n, 256, 152 * 16), 256, 0, (cudaStream_t)stream>>>(n, rho, sigma);
   VT_CUDA_TRY(cudaGetLastError());
   return VT_OK;
@@ -251,6 +257,7 @@ vt_status vt_sigma_from_rho_bwd(int64_t n, const float* sigma, const float* grad
                                 void* stream) {
   if (n < 0 || (n > 0 && (!sigma || !grad_sigma || !grad_rho))) return VT_ERR_INVALID_ARG;
   if (n == 0) return VT_OK;
+  vt_note_launch();
   k_mul<<<vt_grid(n, 256, 152 * 16), 256, 0, (cudaStream_t)stream>>>(n, grad_sigma, sigma, grad_rho);
   VT_CUDA_TRY(cudaGetLastError());
   return VT_OK;

@@ -79,6 +79,12 @@ constexpr int kPatchH = 8 / VT_ST_W;  // tile rows of a patch
 #define VT_NBR_UNROLL 8
 #endif
 constexpr int kNbrUnroll = VT_NBR_UNROLL;
+// 1: stage the neighbour records of a cell that all 32 lanes of a warp share
+// in shared memory (kStageCap records at most per warp)
+#ifndef VT_STAGE
+#define VT_STAGE 0
+#endif
+constexpr int kStageCap = 64;
 
 struct Scene {
   const vt_cell* __restrict__ cell;
@@ -552,6 +558,9 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE, APP, DIST>::minb)
     k_walk(Scene S, RP P, const float* __restrict__ O, const float* __restrict__ D,
            const int32_t* __restrict__ anchor_cell, float* __restrict__ rgb_out, float* __restrict__ T_out,
            int32_t* __restrict__ steps_out, Grad G, Trace TR) {
+#if VT_STAGE
+  __shared__ float4 stage[8][kStageCap];  // per warp: neighbour records of its shared cell
+#endif
   int anchor = 0;
   const int64_t ray = ray_of_thread(P, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, anchor);
   if (ray < 0) return;
@@ -665,9 +674,8 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE, APP, DIST>::minb)
       // Keeping the FP64 call out of the unrolled loop: 350.5 -> 379.3 Mrays/s
       // fwd+bwd on 3M sites / 4 views.
       bool grazed = false;
-#pragma unroll kNbrUnroll
-      for (int p = m.x; p < m.y; ++p) {
-        const float4 q = nbr_record<HALF>(S, p);
+      // one neighbour record q = {n, j}: keep its forward crossing if nearer
+      auto consider = [&](const float4 q) {
         const float den = __fmaf_rn(q.x, d.x, __fmaf_rn(q.y, d.y, __fmul_rn(q.z, d.z)));
         // backward-facing planes (den < -Gc) are dropped before the numerator
         // n.(r + n/2) is formed: the rays of a tile mostly agree on them
@@ -682,6 +690,31 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE, APP, DIST>::minb)
         } else if (den >= -Gc) {
           grazed = true;
         }
+      };
+#if VT_STAGE
+      // Warp-shared cell (Sec. 5.6 warp-coherent tiles): when all 32 lanes of
+      // the warp are in the same cell, its neighbour records are read once
+      // into shared memory with one coalesced load and every lane searches
+      // them there. The test is warp-uniform (all lanes active and equal), so
+      // the whole warp takes the same branch and the __syncwarp()s are
+      // reached by all 32 lanes. Same arithmetic on the same values as the
+      // other branch: the decisions do not depend on which branch ran.
+      bool staged = false;
+      if (!HALF && __activemask() == 0xffffffffu)
+        staged = __match_any_sync(0xffffffffu, cell) == 0xffffffffu && m.y - m.x <= kStageCap;
+      if (staged) {
+        float4* buf = stage[threadIdx.x >> 5];
+        const int deg = m.y - m.x;
+        for (int q = threadIdx.x & 31; q < deg; q += 32) buf[q] = __ldg(S.nbr + m.x + q);
+        __syncwarp();
+#pragma unroll kNbrUnroll
+        for (int p = 0; p < deg; ++p) consider(buf[p]);
+        __syncwarp();  // every lane has read buf before the next step refills it
+      } else
+#endif
+      {
+#pragma unroll kNbrUnroll
+        for (int p = m.x; p < m.y; ++p) consider(nbr_record<HALF>(S, p));
       }
       if (grazed) {
         for (int p = m.x; p < m.y; ++p) {
@@ -1119,7 +1152,9 @@ vt_status anchors(vt_scene* s, const Scene& S, const RP& P, const float* o, cuda
   if (na < 1 || na > VT_MAX_ANCHORS) return VT_ERR_INVALID_ARG;
   VT_CUDA_TRY(cudaMemsetAsync(s->anchor_key, 0xff, na * sizeof(unsigned long long), st));
   dim3 g(vt_grid(s->n, 256, 152 * 2), na);
+  vt_note_launch();
   k_anchor_nn<<<g, 256, 0, st>>>(S, P, o, s->anchor_key);
+  vt_note_launch();
   k_anchor_refine<<<1, 64, 0, st>>>(S, P, o, na, s->inv, s->anchor_key, s->anchor_cell, P.max_steps);
   VT_CUDA_TRY(cudaGetLastError());
   return VT_OK;
@@ -1128,6 +1163,7 @@ vt_status anchors(vt_scene* s, const Scene& S, const RP& P, const float* o, cuda
 template <int MODE, int APP, int DIST, int HALF = 0>
 void launch_walk_app(vt_scene* s, const Scene& S, const RP& P, const float* o, const float* d, float* rgb, float* T,
                      int32_t* steps, Grad G, Trace TR, cudaStream_t st, int g) {
+  vt_note_launch();
   if (s->dtype == VT_F32)
     k_walk<MODE, VT_F32, APP, DIST, HALF><<<g, 256, 0, st>>>(S, P, o, d, s->anchor_cell, rgb, T, steps, G, TR);
   else if (s->dtype == VT_F16)
@@ -1249,6 +1285,7 @@ vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float
     if (r != VT_OK) return r;
   }
   // always launched: it also re-zeroes the flagged cells' texel scratch
+  vt_note_launch();
   k_grad_out<<<vt_grid(s->n * 32, 256, 152 * 16), 256, 0, st>>>(s->n, (int)RR, s->cell, s->g_cell, s->g_tex,
                                                                   grad_sites, grad_sigma, grad_tex, s->g_tex_vd,
                                                                   grad_tex_vd, s->g_touched);
@@ -1339,6 +1376,7 @@ vt_status vt_render_bwd_static(vt_scene* s, int64_t n_rays, const float* o, cons
     if (r != VT_OK) return r;
   }
   if (grad_sites || grad_sigma || grad_tex) {
+    vt_note_launch();
     k_grad_out<<<vt_grid(s->n * 32, 256, 152 * 16), 256, 0, st>>>(s->n, (int)RR, s->cell, g_cell, g_tex,
                                                                     grad_sites, grad_sigma, grad_tex, nullptr,
                                                                     nullptr, nullptr);

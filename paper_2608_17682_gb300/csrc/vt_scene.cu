@@ -195,6 +195,7 @@ vt_status fill_half_offsets(vt_scene* s, cudaStream_t st) {
   unsigned long long hbad = 0;
   cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned long long), st);
   if (e == cudaSuccess) {
+    vt_note_launch();
     k_fill_nbr_h<<<vt_grid(s->E, 256, 152 * 32), 256, 0, st>>>(s->E, s->nbr, s->nbr_h, bad);
     e = cudaGetLastError();
   }
@@ -244,6 +245,7 @@ vt_status pack_tex(vt_scene* s, const float* tex, cudaStream_t st, void* dst = n
   int64_t total = s->n * (int64_t)s->R * s->R;
   int g = vt_grid(total, 256, 152 * 64);
   void* out = dst ? dst : s->tex;
+  vt_note_launch();
   if (s->dtype == VT_F32)
     k_pack_tex<VT_F32><<<g, 256, 0, st>>>(s->n, s->R * s->R, s->perm, tex, out);
   else if (s->dtype == VT_F16)
@@ -267,12 +269,14 @@ vt_status validate(int64_t n, const float* sites, const float* sigma, const int6
   cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned), st);
   int g = vt_grid(n, 256, 152 * 32);
   if (e == cudaSuccess) {
+    vt_note_launch();
     k_validate_nodes<<<g, 256, 0, st>>>(n, sites, sigma, off, E, bad);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess && hbad == 0 && off && (idx || E == 0)) {
+    vt_note_launch();
     k_validate_rows<<<g, 256, 0, st>>>(n, off, idx, bad);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
@@ -334,6 +338,7 @@ vt_status create_impl(const vt_scene_desc* dsc, cudaStream_t st, vt_scene* s) {
   const int nb = 256;
   float* part = nullptr;
   VT_CUDA_TRY(cudaMalloc(&part, nb * 6 * sizeof(float)));
+  vt_note_launch();
   k_bbox<<<nb, 256, 0, st>>>(n, dsc->sites, part);
   float hp[nb * 6];
   cudaError_t e = cudaMemcpyAsync(hp, part, sizeof(hp), cudaMemcpyDeviceToHost, st);
@@ -365,6 +370,7 @@ vt_status create_impl(const vt_scene_desc* dsc, cudaStream_t st, vt_scene* s) {
       break;
     }
     int g = vt_grid(n, 256, 152 * 32);
+    vt_note_launch();
     k_morton<<<g, 256, 0, st>>>(n, dsc->sites, lo3, sc3, code, ids);
     cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, code, code2, ids, s->perm, (int)n, 0, 63, st);
     cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, deg, beg, (int)n, st);
@@ -383,14 +389,19 @@ vt_status create_impl(const vt_scene_desc* dsc, cudaStream_t st, vt_scene* s) {
       rs = VT_ERR_CUDA;
       break;
     }
+    vt_note_launch();
     k_inverse<<<g, 256, 0, st>>>(n, s->perm, s->inv);
+    vt_note_launch();
     k_degree<<<g, 256, 0, st>>>(n, s->perm, dsc->adj_offsets, deg);
     if (cub::DeviceScan::ExclusiveSum(tmp, tmp_bytes, deg, beg, (int)n, st) != cudaSuccess) {
       rs = VT_ERR_CUDA;
       break;
     }
+    vt_note_launch();
     k_fill_cells<<<g, 256, 0, st>>>(n, s->perm, dsc->sites, dsc->sigma, beg, deg, s->cell, 0);
+    vt_note_launch();
     k_fill_nbr<<<g, 256, 0, st>>>(n, s->cell, dsc->adj_offsets, dsc->adj_indices, s->inv, s->nbr);
+    vt_note_launch();
     k_cell_nmax<<<g, 256, 0, st>>>(n, s->cell, s->nbr);
     rs = fill_half_offsets(s, st);
     if (rs != VT_OK) break;
@@ -471,9 +482,12 @@ vt_status vt_scene_update(vt_scene* s, const float* sites, const float* sigma, c
     vt_status v = validate(s->n, sites, sigma, nullptr, nullptr, 0, st);
     if (v != VT_OK) return v;
     int g = vt_grid(s->n, 256, 152 * 32);
+    vt_note_launch();
     k_fill_cells<<<g, 256, 0, st>>>(s->n, s->perm, sites, sigma, nullptr, nullptr, s->cell, 1);
     if (sites) {
+      vt_note_launch();
       k_refresh_nbr<<<g, 256, 0, st>>>(s->n, s->cell, s->nbr);
+      vt_note_launch();
       k_cell_nmax<<<g, 256, 0, st>>>(s->n, s->cell, s->nbr);
     }
     VT_CUDA_TRY(cudaGetLastError());

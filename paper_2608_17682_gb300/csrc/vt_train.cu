@@ -143,6 +143,7 @@ vt_status vt_sample_rays(int64_t n_pool, const float* o_pool, const float* d_poo
   if (n_pool < 0 || n < 0 || n > n_pool) return VT_ERR_INVALID_ARG;
   if (n == 0) return VT_OK;
   if (!o_pool || !d_pool || !o || !d || (y && !y_pool)) return VT_ERR_INVALID_ARG;
+  vt_note_launch();
   k_sample<<<vt_grid(n, 256, 152 * 16), 256, 0, (cudaStream_t)stream>>>(n_pool, n, seed, o_pool, d_pool, y_pool, o,
                                                                          d, y, idx_out);
   VT_CUDA_TRY(cudaGetLastError());
@@ -155,6 +156,7 @@ vt_status vt_smooth_l1_loss(int64_t n, const float* rgb, const float* target, fl
   cudaStream_t st = (cudaStream_t)stream;
   VT_CUDA_TRY(cudaMemsetAsync(loss_out, 0, sizeof(float), st));
   if (n == 0) return VT_OK;
+  vt_note_launch();
   k_smooth_l1<<<vt_grid(3 * n, 256, 152 * 8), 256, 0, st>>>(3 * n, 1.0f / (float)(3 * n), beta, rgb, target,
                                                             grad_out, loss_out);
   VT_CUDA_TRY(cudaGetLastError());
@@ -169,6 +171,7 @@ vt_status vt_texture_regularizers(int64_t n_cells, int32_t tex_res, const float*
   cudaStream_t st = (cudaStream_t)stream;
   VT_CUDA_TRY(cudaMemsetAsync(loss_out, 0, sizeof(float), st));
   if (n_cells == 0) return VT_OK;
+  vt_note_launch();
   k_tex_reg<<<vt_grid(n_cells * 32, 256, 152 * 8), 256, 0, st>>>(n_cells, tex_res * tex_res, lambda_vd, lambda_mean,
                                                                   tex, tex_vd, grad_tex, grad_tex_vd, loss_out);
   VT_CUDA_TRY(cudaGetLastError());
@@ -182,6 +185,7 @@ vt_status vt_adam_step(int64_t n, float* param, const float* grad, float* m, flo
   if (n == 0) return VT_OK;
   const float c1 = (float)(1.0 - pow((double)beta1, (double)step));
   const float c2 = (float)(1.0 - pow((double)beta2, (double)step));
+  vt_note_launch();
   k_adam<<<vt_grid(n, 256, 152 * 16), 256, 0, (cudaStream_t)stream>>>(n, param, grad, m, v, lr, beta1, beta2, eps,
                                                                        c1, c2);
   VT_CUDA_TRY(cudaGetLastError());
