@@ -325,7 +325,7 @@ def run_ours(args, ws, rank, local):
         params.walk_events[0] = pair[0].cuda_event if pair else None
         params.walk_events[1] = pair[1].cuda_event if pair else None
 
-    def step(scene, marks=None, fwd_only=False):
+    def step(scene, marks=None, fwd_only=False, scene_order=False):
         # marks: 4 events around the fwd / bwd calls, then 4 the library
         # records around the forward and backward walk kernels themselves
         api.generate_rays(cams, out=(o, d, tm))
@@ -342,7 +342,10 @@ def run_ours(args, ws, rank, local):
         if marks:
             marks[2].record(stream)
             walk_events(marks[6:8])
-        api.render_bwd(scene, o, d, params, rgb, grad, time=tm, out=(gs, gsig, gt), residual=res)
+        if scene_order:  # gradients left in the scene's cell order (no permute)
+            api.render_bwd_scene_order(scene, o, d, params, rgb, grad, time=tm, residual=res)
+        else:
+            api.render_bwd(scene, o, d, params, rgb, grad, time=tm, out=(gs, gsig, gt), residual=res)
         walk_events(None)
         if marks:
             marks[3].record(stream)
@@ -354,12 +357,12 @@ def run_ours(args, ws, rank, local):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def timed(scene, K, fwd_only=False, walks=None):
+    def timed(scene, K, fwd_only=False, walks=None, scene_order=False):
         """K steps, L2 flushed between steps (outside the timed events). If
         `walks` is a dict it receives the mean forward / backward walk-kernel
         times (events recorded by the library around the kernel launches)."""
         for _ in range(args.warmup):
-            step(scene, fwd_only=fwd_only)
+            step(scene, fwd_only=fwd_only, scene_order=scene_order)
         barrier()
         st, en, marks = [], [], []
         for _ in range(K):
@@ -369,7 +372,7 @@ def run_ours(args, ws, rank, local):
             for e in m[4:]:
                 e.record(stream)  # creates the event handle the library records into
             a.record(stream)
-            step(scene, m, fwd_only=fwd_only)
+            step(scene, m, fwd_only=fwd_only, scene_order=scene_order)
             b.record(stream)
             st.append(a)
             en.append(b)
@@ -412,6 +415,13 @@ def run_ours(args, ws, rank, local):
     extra = {}
     ms_f, fwd_only_fwd, _ = timed(main, max(3, args.steps // 2), fwd_only=True)
     extra["fwd_only_mrays_s"] = round(n_rays / (ms_f * 1e-3) / 1e6 * ws, 2)
+    # the same step with the gradients left in the scene's cell order
+    # (vt_render_bwd_scene_order: no permute to user order)
+    w_so = {}
+    m_s, m_f, m_b = timed(main, max(3, args.steps // 2), walks=w_so, scene_order=True)
+    extra["scene_order_grads"] = {"fwd_bwd_mrays_s": round(n_rays / (m_s * 1e-3) / 1e6 * ws, 2),
+                                  "ms_bwd": round(m_b, 3), "ms_bwd_walk_kernel": round(w_so["bwd"], 4),
+                                  "ms_bwd_outside_walk": round(m_b - w_so["bwd"], 4)}
     grads_by_dtype = {args.tex: grads_main}
     for t in dtypes[1:]:
         w_t = {}

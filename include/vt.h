@@ -278,6 +278,31 @@ vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float
                         const float* dist_out, const float* grad_rgb, const float* grad_dist, float* grad_sites,
                         float* grad_sigma, float* grad_tex, float* grad_tex_vd, void* stream);
 
+/* Backward render that leaves the gradients in the scene's own cell order
+ * (the Morton order of vt_scene_create; Sec. 5.6 keeps cells in that order)
+ * instead of permuting them to user order: same walk, arguments and numerics
+ * as vt_render_bwd, minus the permute, which writes the dense user-order
+ * arrays (about 1 ms and 4 GB of traffic for 3M cells with 8x8 textures). On
+ * success it sets *grad_cell, *grad_tex and (if not NULL) *grad_tex_vd to
+ * DEVICE arrays owned by the scene:
+ *   grad_cell [N][4]      {dL/ds_x, dL/ds_y, dL/ds_z, dL/dsigma} of cell k,
+ *   grad_tex  [N][R][R][4] RGBA texel gradients (A is 0), grad_tex_vd the same
+ *                         for the view-dependent texture (appearance 1; NULL
+ *                         when the scene has none),
+ * where cell k is the user's site vt_scene_permutation()[k]. They hold this
+ * call's gradients until the next backward call on the scene (of either
+ * kind) or its destruction; the next call re-zeroes only the texel blocks
+ * this one wrote. Read them on `stream` (or after synchronising it). */
+vt_status vt_render_bwd_scene_order(vt_scene* s, int64_t n_rays, const float* o, const float* d, const float* time,
+                                    const vt_render_params* p, const float* rgb_out, const float* rgb_residual,
+                                    const float* dist_out, const float* grad_rgb, const float* grad_dist,
+                                    const float** grad_cell, const float** grad_tex, const float** grad_tex_vd,
+                                    void* stream);
+
+/* The scene's cell order: perm [N] DEVICE int32, perm[k] = user id of cell k
+ * (copied on `stream`). */
+vt_status vt_scene_permutation(const vt_scene* s, int32_t* perm, void* stream);
+
 /* Allocation-free backward (no counterpart in the paper). Same arguments,
  * outputs and numerics as vt_render_bwd without a colour residual or distortion
  * loss, appearance 0 only (appearance 1 returns VT_ERR_UNSUPPORTED), for callers that may not allocate

@@ -21,7 +21,7 @@ VT_CAM_PINHOLE, VT_CAM_FISHEYE_EQUIDIST, VT_CAM_ROLLING_SHUTTER, VT_CAM_THIN_LEN
 # every symbol include/vt.h declares
 EXPORTS = ["vt_render_params_default", "vt_scene_create", "vt_scene_update", "vt_scene_destroy", "vt_scene_info",
            "vt_scene_get_error", "vt_camera_n_rays", "vt_generate_rays", "vt_render_fwd", "vt_render_bwd",
-           "vt_render_bwd_static", "vt_trace_cells", "vt_l2_loss", "vt_average_samples", "vt_average_samples_bwd", "vt_sigma_from_rho",
+           "vt_render_bwd_static", "vt_render_bwd_scene_order", "vt_scene_permutation", "vt_trace_cells", "vt_l2_loss", "vt_average_samples", "vt_average_samples_bwd", "vt_sigma_from_rho",
            "vt_sigma_from_rho_bwd", "vt_sample_rays", "vt_smooth_l1_loss", "vt_texture_regularizers", "vt_adam_step",
            "vt_kernel_launches", "vt_stream_read", "vt_status_str"]
 
@@ -75,6 +75,8 @@ def _load():
         "vt_render_fwd": ([P, I64, P, P, P, P, P, P, P, P, P, P], C.c_int),
         "vt_render_bwd": ([P, I64, P, P, P, P, P, P, P, P, P, P, P, P, P, P], C.c_int),
         "vt_render_bwd_static": ([P, I64, P, P, P, P, P, P, P, P, P, P], C.c_int),
+        "vt_render_bwd_scene_order": ([P, I64, P, P, P, P, P, P, P, P, P, P, P, P, P], C.c_int),
+        "vt_scene_permutation": ([P, P, P], C.c_int),
         "vt_trace_cells": ([P, I64, P, P, P, I32, P, P, P, P], C.c_int),
         "vt_l2_loss": ([I64, P, P, P, P, P], C.c_int),
         "vt_average_samples": ([I64, I32, P, P, P], C.c_int),
@@ -179,6 +181,24 @@ def vt_render_bwd_static(scene: int, n_rays: int, o: int, d: int, time: int, par
                                    C.byref(params), C.c_void_p(rgb), C.c_void_p(grad_rgb), C.c_void_p(grad_sites),
                                    C.c_void_p(grad_sigma), C.c_void_p(grad_tex), C.c_void_p(stream)),
           "vt_render_bwd_static")
+
+
+def vt_render_bwd_scene_order(scene: int, n_rays: int, o: int, d: int, time: int, params: vt_render_params,
+                              rgb: int, rgb_residual: int, dist: int, grad_rgb: int, grad_dist: int, want_vd: bool,
+                              stream: int):
+    """Returns the device addresses (grad_cell, grad_tex, grad_tex_vd or 0) of
+    the scene-owned, scene-order gradients."""
+    gc, gt, gv = C.c_void_p(), C.c_void_p(), C.c_void_p()
+    check(lib.vt_render_bwd_scene_order(C.c_void_p(scene), n_rays, C.c_void_p(o), C.c_void_p(d), C.c_void_p(time),
+                                        C.byref(params), C.c_void_p(rgb), C.c_void_p(rgb_residual), C.c_void_p(dist),
+                                        C.c_void_p(grad_rgb), C.c_void_p(grad_dist), C.byref(gc), C.byref(gt),
+                                        C.byref(gv) if want_vd else None, C.c_void_p(stream)),
+          "vt_render_bwd_scene_order")
+    return gc.value or 0, gt.value or 0, gv.value or 0
+
+
+def vt_scene_permutation(scene: int, perm: int, stream: int):
+    check(lib.vt_scene_permutation(C.c_void_p(scene), C.c_void_p(perm), C.c_void_p(stream)), "vt_scene_permutation")
 
 
 def vt_trace_cells(scene: int, n_rays: int, o: int, d: int, params: vt_render_params, max_cells: int, cells: int,

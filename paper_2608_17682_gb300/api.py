@@ -95,6 +95,12 @@ class Scene:
             raise ValueError("tex_vd given for a scene built without one")
         _vt.vt_scene_update(self.handle, *[_ptr(x) for x in keep], _stream())
 
+    def permutation(self):
+        """perm [N] int32 on the device: perm[k] = user id of the scene's cell k."""
+        perm = torch.empty(self.n, dtype=torch.int32, device=self.device)
+        _vt.vt_scene_permutation(self.handle, perm.data_ptr(), _stream())
+        return perm
+
     def get_error(self):
         """(status, fp64_rechecks) since the last call; synchronises the stream."""
         return _vt.vt_scene_get_error(self.handle, _stream())
@@ -216,6 +222,39 @@ def render_bwd(scene: Scene, o, d, params, rgb, grad_rgb, time=None, out=None, n
                       _ptr(residual), _ptr(dist), grad_rgb.data_ptr(), _ptr(grad_dist), _ptr(gs),
                       _ptr(gsig), _ptr(gt), _ptr(tex_vd_out), _stream())
     return gs, gsig, gt
+
+
+class _DeviceView:
+    """A scene-owned device array seen through __cuda_array_interface__, so
+    that torch can wrap it without a copy (the scene keeps ownership)."""
+
+    def __init__(self, ptr, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f4", "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+def render_bwd_scene_order(scene: Scene, o, d, params, rgb, grad_rgb, time=None, residual=None, dist=None,
+                           grad_dist=None):
+    """Backward render with the gradients left in the scene's cell order:
+    returns (grad_cell [N,4] = (dL/ds, dL/dsigma), grad_tex [N,R,R,4] RGBA,
+    grad_tex_vd [N,R,R,4] or None), torch views of scene-owned memory valid
+    until the next backward call on the scene. Cell k is the user's site
+    scene.permutation()[k]."""
+    n, N, R = o.shape[0], scene.n, scene.R
+    grad_rgb = grad_rgb.contiguous()
+    for t, name, shape, opt in ((o, "o", (n, 3), False), (d, "d", (n, 3), False), (rgb, "rgb", (n, 3), False),
+                                (grad_rgb, "grad_rgb", (n, 3), False), (time, "time", (n,), True),
+                                (residual, "residual", (n, 3), True), (dist, "dist", (n, 3), True),
+                                (grad_dist, "grad_dist", (n,), True)):
+        _arr(t, name, shape, optional=opt)
+    gc, gt, gv = _vt.vt_render_bwd_scene_order(scene.handle, n, o.data_ptr(), d.data_ptr(), _ptr(time), params,
+                                               rgb.data_ptr(), _ptr(residual), _ptr(dist), grad_rgb.data_ptr(),
+                                               _ptr(grad_dist), scene.has_tex_vd, _stream())
+    dev = o.device
+    cell = torch.as_tensor(_DeviceView(gc, (N, 4)), device=dev)
+    tex = torch.as_tensor(_DeviceView(gt, (N, R, R, 4)), device=dev)
+    vd = torch.as_tensor(_DeviceView(gv, (N, R, R, 4)), device=dev) if gv else None
+    return cell, tex, vd
 
 
 def trace_cells(scene: Scene, o, d, params, max_cells=512):

@@ -57,6 +57,9 @@ struct vt_scene {
   // g_tex_clean: the texel scratch is zero outside the flagged cells
   uint8_t* g_touched = nullptr;
   bool g_tex_clean = false;
+  // g_held: the flagged cells' blocks hold the sums of a scene-order backward
+  // (vt_render_bwd_scene_order) that the caller may still read
+  bool g_held = false;
 };
 
 // Kernels this library has launched since the process started (all devices

@@ -44,7 +44,10 @@ enum Mode { FWD = 0, BWD = 1, TRACE = 2 };
 #define VT_FWD_MINB 4
 #endif
 #ifndef VT_BWD_MINB
-#define VT_BWD_MINB 4  // plain backward (appearance 0, no distortion): 349.5 vs 345.9 Mrays/s at 3
+// plain backward (appearance 0, no distortion): with the branch-free exit
+// search, 3 blocks/SM (80 registers) runs 5.11 ms against 5.31 ms at 4 (64
+// registers, more spills) on 3M sites / 4 views
+#define VT_BWD_MINB 3
 #endif
 #ifndef VT_BWD_MINB_EXT
 #define VT_BWD_MINB_EXT 3  // backward with the paper's appearance model or the distortion loss
@@ -669,27 +672,28 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE, APP, DIST>::minb)
       const float Gc = __fmul_rn(Gd, __int_as_float(m.w));
       float bn = 1.f, bd = 0.f;  // best dt = bn / bd (bd == 0: none yet)
       int bj = -1;
-      // grazing planes (|n.d| <= Gc) are only noted in the hot loop; their FP64
-      // recheck runs in a second pass over the cell when one was seen (rare).
-      // Keeping the FP64 call out of the unrolled loop: 350.5 -> 379.3 Mrays/s
-      // fwd+bwd on 3M sites / 4 views.
-      bool grazed = false;
-      // one neighbour record q = {n, j}: keep its forward crossing if nearer
+      // grazing planes (|n.d| <= Gc) are only noted in the hot loop, through
+      // the running minimum of |n.d|; their FP64 recheck runs in a second pass
+      // over the cell when there is one (rare). Keeping the FP64 call out of
+      // the unrolled loop: 350.5 -> 379.3 Mrays/s fwd+bwd on 3M sites / 4 views.
+      float mind = INFINITY;
+      // One neighbour record q = {n, j}: keep its forward crossing if nearer.
+      // The body has no branch: every plane's numerator n.(r + n/2) is formed
+      // and the candidate kept by a predicated select. On 3M sites / 4 views
+      // this cut the forward walk from 4.21 to 3.18 ms and the backward from
+      // 6.29 to 5.30 ms against a body that branched on n.d first and noted
+      // grazing planes in an else branch (the branches inside the unrolled
+      // loop had cost more than the arithmetic they skipped).
       auto consider = [&](const float4 q) {
         const float den = __fmaf_rn(q.x, d.x, __fmaf_rn(q.y, d.y, __fmul_rn(q.z, d.z)));
-        // backward-facing planes (den < -Gc) are dropped before the numerator
-        // n.(r + n/2) is formed: the rays of a tile mostly agree on them
-        if (den > Gc) {
-          const float num = __fmaf_rn(q.x, __fmaf_rn(0.5f, q.x, r.x),
-                                      __fmaf_rn(q.y, __fmaf_rn(0.5f, q.y, r.y), __fmul_rn(q.z, __fmaf_rn(0.5f, q.z, r.z))));
-          if (__fmul_rn(num, bd) < __fmul_rn(bn, den)) {
-            bn = num;
-            bd = den;
-            bj = __float_as_int(q.w);
-          }
-        } else if (den >= -Gc) {
-          grazed = true;
+        const float num = __fmaf_rn(q.x, __fmaf_rn(0.5f, q.x, r.x),
+                                    __fmaf_rn(q.y, __fmaf_rn(0.5f, q.y, r.y), __fmul_rn(q.z, __fmaf_rn(0.5f, q.z, r.z))));
+        if (den > Gc && __fmul_rn(num, bd) < __fmul_rn(bn, den)) {
+          bn = num;
+          bd = den;
+          bj = __float_as_int(q.w);
         }
+        mind = fminf(mind, fabsf(den));
       };
 #if VT_STAGE
       // Warp-shared cell (Sec. 5.6 warp-coherent tiles): when all 32 lanes of
@@ -716,6 +720,8 @@ __global__ void __launch_bounds__(256, WalkBounds<MODE, APP, DIST>::minb)
 #pragma unroll kNbrUnroll
         for (int p = m.x; p < m.y; ++p) consider(nbr_record<HALF>(S, p));
       }
+      // grazing planes (|n.d| <= Gc) of this cell
+      const bool grazed = mind <= Gc;
       if (grazed) {
         for (int p = m.x; p < m.y; ++p) {
           const float4 q = nbr_record<HALF>(S, p);
@@ -1211,6 +1217,82 @@ vt_status launch_walk(vt_scene* s, const Scene& S, const RP& P, const float* o, 
   return VT_OK;
 }
 
+// Gradient scratch of a scene, ready for a backward walk: allocated on first
+// use; cell gradients cleared; texel scratch zero everywhere (fully cleared
+// after first use or an interrupted call, else only the blocks a scene-order
+// backward left holding sums, see vt_render_bwd_scene_order).
+__global__ void k_rezero(int64_t n, int RR, float4* g_tex, float4* g_tex_vd, uint8_t* touched) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+    if (!touched[i]) continue;  // warp-uniform
+    for (int t = lane; t < RR; t += 32) {
+      g_tex[i * RR + t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (g_tex_vd) g_tex_vd[i * RR + t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncwarp();
+    if (lane == 0) touched[i] = 0;
+  }
+}
+
+vt_status prepare_scratch(vt_scene* s, cudaStream_t st) {
+  const int64_t RR = (int64_t)s->R * s->R;
+  if (!s->g_cell) VT_CUDA_TRY(cudaMalloc(&s->g_cell, s->n * sizeof(float4)));
+  if (!s->g_tex) {
+    s->g_tex_clean = false;
+    VT_CUDA_TRY(cudaMalloc(&s->g_tex, s->n * RR * sizeof(float4)));
+  }
+  if (s->tex_vd && !s->g_tex_vd) {
+    s->g_tex_clean = false;
+    VT_CUDA_TRY(cudaMalloc(&s->g_tex_vd, s->n * RR * sizeof(float4)));
+  }
+  if (!s->g_touched) {
+    s->g_tex_clean = false;
+    VT_CUDA_TRY(cudaMalloc(&s->g_touched, s->n));
+  }
+  VT_CUDA_TRY(cudaMemsetAsync(s->g_cell, 0, s->n * sizeof(float4), st));
+  if (!s->g_tex_clean) {
+    // first use, or a previous call stopped before its permute: clear everything
+    VT_CUDA_TRY(cudaMemsetAsync(s->g_tex, 0, s->n * RR * sizeof(float4), st));
+    if (s->g_tex_vd) VT_CUDA_TRY(cudaMemsetAsync(s->g_tex_vd, 0, s->n * RR * sizeof(float4), st));
+    VT_CUDA_TRY(cudaMemsetAsync(s->g_touched, 0, s->n, st));
+  } else if (s->g_held) {
+    vt_note_launch();
+    k_rezero<<<vt_grid(s->n * 32, 256, 152 * 16), 256, 0, st>>>(s->n, (int)RR, s->g_tex, s->g_tex_vd, s->g_touched);
+    VT_CUDA_TRY(cudaGetLastError());
+  }
+  s->g_tex_clean = false;  // until the call that follows finishes enqueueing
+  s->g_held = false;
+  return VT_OK;
+}
+
+// The backward walk shared by vt_render_bwd and vt_render_bwd_scene_order:
+// checks, scratch preparation, start cells and the re-traversal into the
+// Morton-ordered scratch (cells it adds texel gradients to are flagged).
+vt_status backward_walk(vt_scene* s, int64_t n_rays, const float* o, const float* d, const vt_render_params* p,
+                        const float* rgb_out, const float* rgb_residual, const float* dist_out, const float* grad_rgb,
+                        const float* grad_dist, cudaStream_t st) {
+  if (!s || n_rays < 0 || (n_rays > 0 && (!o || !d || !rgb_out || !grad_rgb))) return VT_ERR_INVALID_ARG;
+  if (grad_dist && !dist_out) return VT_ERR_INVALID_ARG;
+  if (s->nbr_h) return VT_ERR_UNSUPPORTED;  // FP16-offset scenes are forward only
+  RP P;
+  vt_status r = make_rp(s, n_rays > 0 ? n_rays : 0, p, P);
+  if (r != VT_OK && n_rays > 0) return r;
+  if (grad_dist && n_rays > 0 && !(P.t_near >= 0.f)) return VT_ERR_INVALID_ARG;
+  r = prepare_scratch(s, st);
+  if (r != VT_OK) return r;
+  if (n_rays == 0) return VT_OK;
+  Scene S = scene_view(s);
+  r = anchors(s, S, P, o, st);
+  if (r != VT_OK) return r;
+  Grad G{s->g_cell, s->g_tex, s->g_tex_vd, rgb_out, rgb_residual, grad_rgb, nullptr, nullptr, s->g_touched};
+  if (grad_dist) {
+    G.dist = const_cast<float*>(dist_out);  // read only in the backward
+    G.gdist = grad_dist;
+  }
+  return launch_walk<BWD>(s, S, P, o, d, nullptr, nullptr, nullptr, G, Trace{}, st, p);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1241,56 +1323,46 @@ vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float
                         const float* dist_out, const float* grad_rgb, const float* grad_dist, float* grad_sites,
                         float* grad_sigma, float* grad_tex, float* grad_tex_vd, void* stream) {
   (void)time;
-  if (!s || n_rays < 0 || (n_rays > 0 && (!o || !d || !rgb_out || !grad_rgb))) return VT_ERR_INVALID_ARG;
-  if (grad_tex_vd && !s->tex_vd) return VT_ERR_INVALID_ARG;
-  if (grad_dist && !dist_out) return VT_ERR_INVALID_ARG;
-  if (s->nbr_h) return VT_ERR_UNSUPPORTED;  // FP16-offset scenes are forward only
-  RP P;
-  vt_status r = make_rp(s, n_rays > 0 ? n_rays : 0, p, P);
-  if (r != VT_OK && n_rays > 0) return r;
-  if (grad_dist && n_rays > 0 && !(P.t_near >= 0.f)) return VT_ERR_INVALID_ARG;
+  if (grad_tex_vd && s && !s->tex_vd) return VT_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  const int64_t RR = (int64_t)s->R * s->R;
-  if (!s->g_cell) VT_CUDA_TRY(cudaMalloc(&s->g_cell, s->n * sizeof(float4)));
-  if (!s->g_tex) {
-    s->g_tex_clean = false;
-    VT_CUDA_TRY(cudaMalloc(&s->g_tex, s->n * RR * sizeof(float4)));
-  }
-  if (s->tex_vd && !s->g_tex_vd) {
-    s->g_tex_clean = false;
-    VT_CUDA_TRY(cudaMalloc(&s->g_tex_vd, s->n * RR * sizeof(float4)));
-  }
-  if (!s->g_touched) {
-    s->g_tex_clean = false;
-    VT_CUDA_TRY(cudaMalloc(&s->g_touched, s->n));
-  }
-  VT_CUDA_TRY(cudaMemsetAsync(s->g_cell, 0, s->n * sizeof(float4), st));
-  if (!s->g_tex_clean) {
-    // first use, or a previous call stopped before its permute: clear everything
-    VT_CUDA_TRY(cudaMemsetAsync(s->g_tex, 0, s->n * RR * sizeof(float4), st));
-    if (s->g_tex_vd) VT_CUDA_TRY(cudaMemsetAsync(s->g_tex_vd, 0, s->n * RR * sizeof(float4), st));
-    VT_CUDA_TRY(cudaMemsetAsync(s->g_touched, 0, s->n, st));
-  }
-  s->g_tex_clean = false;  // until this call's permute is enqueued
-  Scene S = scene_view(s);
-  if (n_rays > 0) {
-    r = anchors(s, S, P, o, st);
-    if (r != VT_OK) return r;
-    Grad G{s->g_cell, s->g_tex, s->g_tex_vd, rgb_out, rgb_residual, grad_rgb, nullptr, nullptr, s->g_touched};
-    if (grad_dist) {
-      G.dist = const_cast<float*>(dist_out);  // read only in the backward
-      G.gdist = grad_dist;
-    }
-    r = launch_walk<BWD>(s, S, P, o, d, nullptr, nullptr, nullptr, G, Trace{}, st, p);
-    if (r != VT_OK) return r;
-  }
+  vt_status r = backward_walk(s, n_rays, o, d, p, rgb_out, rgb_residual, dist_out, grad_rgb, grad_dist, st);
+  if (r != VT_OK) return r;
   // always launched: it also re-zeroes the flagged cells' texel scratch
   vt_note_launch();
-  k_grad_out<<<vt_grid(s->n * 32, 256, 152 * 16), 256, 0, st>>>(s->n, (int)RR, s->cell, s->g_cell, s->g_tex,
-                                                                  grad_sites, grad_sigma, grad_tex, s->g_tex_vd,
-                                                                  grad_tex_vd, s->g_touched);
+  k_grad_out<<<vt_grid(s->n * 32, 256, 152 * 16), 256, 0, st>>>(s->n, (int)(s->R * s->R), s->cell, s->g_cell,
+                                                                  s->g_tex, grad_sites, grad_sigma, grad_tex,
+                                                                  s->g_tex_vd, grad_tex_vd, s->g_touched);
   VT_CUDA_TRY(cudaGetLastError());
   s->g_tex_clean = true;
+  s->g_held = false;
+  return VT_OK;
+}
+
+vt_status vt_render_bwd_scene_order(vt_scene* s, int64_t n_rays, const float* o, const float* d, const float* time,
+                                    const vt_render_params* p, const float* rgb_out, const float* rgb_residual,
+                                    const float* dist_out, const float* grad_rgb, const float* grad_dist,
+                                    const float** grad_cell, const float** grad_tex, const float** grad_tex_vd,
+                                    void* stream) {
+  (void)time;
+  if (!grad_cell || !grad_tex) return VT_ERR_INVALID_ARG;
+  *grad_cell = *grad_tex = nullptr;
+  if (grad_tex_vd) *grad_tex_vd = nullptr;
+  vt_status r = backward_walk(s, n_rays, o, d, p, rgb_out, rgb_residual, dist_out, grad_rgb, grad_dist,
+                              (cudaStream_t)stream);
+  if (r != VT_OK) return r;
+  // the flagged cells' blocks now hold this call's sums; the next backward
+  // call on the scene re-zeroes them first
+  s->g_tex_clean = true;
+  s->g_held = true;
+  *grad_cell = reinterpret_cast<const float*>(s->g_cell);
+  *grad_tex = reinterpret_cast<const float*>(s->g_tex);
+  if (grad_tex_vd) *grad_tex_vd = reinterpret_cast<const float*>(s->g_tex_vd);
+  return VT_OK;
+}
+
+vt_status vt_scene_permutation(const vt_scene* s, int32_t* perm, void* stream) {
+  if (!s || !perm) return VT_ERR_INVALID_ARG;
+  VT_CUDA_TRY(cudaMemcpyAsync(perm, s->perm, s->n * sizeof(int32_t), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
   return VT_OK;
 }
 

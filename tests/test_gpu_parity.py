@@ -906,6 +906,80 @@ def test_backward_scratch_is_clean_between_calls(medium):
     assert a[2].reshape(sc.n, -1)[~touched].abs().max().item() == 0.0
 
 
+def _scene_order_to_user(scene, gc, gt):
+    """Scene-order gradients (float4 cells, RGBA texels) in user order, as the
+    outputs of vt_render_bwd."""
+    perm = scene.permutation().long()
+    gs = torch.empty(scene.n, 3, device=DEV)
+    gsig = torch.empty(scene.n, device=DEV)
+    gtu = torch.empty(scene.n, scene.R, scene.R, 3, device=DEV)
+    gs[perm] = gc[:, :3]
+    gsig[perm] = gc[:, 3]
+    gtu[perm] = gt[..., :3]
+    return gs, gsig, gtu
+
+
+def test_scene_order_backward_against_oracle(medium):
+    """vt_render_bwd_scene_order: the gradients left in the scene's cell order
+    (no permute), mapped back with vt_scene_permutation, against the oracle;
+    repeated calls and a following vt_render_bwd see clean scratch."""
+    sc, osc, o, d, cams = medium
+    base = W.default_params()
+    P = gpu_params(base, img_w=203, img_h=121, n_images=2)
+    _, _, _, flags = O.render(osc, o, d, params=oracle_params(base))
+    ok = (flags & O.BAND_FLAGS) == 0
+    rng = np.random.default_rng(24)
+    g = (rng.normal(size=(len(o), 3)) * ok[:, None]).astype(np.float32)
+    scene = api.Scene.from_workload(sc)
+    to, td, tg = to_dev(o, d, g)
+    rgb, res = fwd_res(scene, to, td, P)
+    gc, gt, gv = api.render_bwd_scene_order(scene, to, td, P, rgb, tg, residual=res)
+    assert gv is None and gc.shape == (sc.n, 4) and gt.shape == (sc.n, sc.R, sc.R, 4)
+    assert scene.get_error()[0] == 0
+    assert gt[..., 3].abs().max().item() == 0.0
+    gs, gsig, gtu = [x.cpu().numpy() for x in _scene_order_to_user(scene, gc, gt)]
+    ogs, ogsig, ogt = O.render_bwd(osc, o, d, g.astype(np.float64), params=oracle_params(base))
+    grad_close(gsig, ogsig, "sigma")
+    grad_close(gtu, ogt, "tex")
+    grad_close(gs, ogs, "sites")
+    # a second scene-order call with other gradients, then the user-order call:
+    # both equal a fresh scene's user-order backward
+    g2 = seeded(len(o), 3, seed=108)
+    gc2, gt2, _ = api.render_bwd_scene_order(scene, to, td, P, rgb, g2, residual=res)
+    second = _scene_order_to_user(scene, gc2, gt2)
+    third = api.render_bwd(scene, to, td, P, rgb, g2, residual=res)
+    fresh = api.render_bwd(api.Scene.from_workload(sc), to, td, P, rgb, g2, residual=res)
+    for a, b, f in zip(second, third, fresh):
+        scale = max(1.0, f.abs().max().item())
+        assert (a - f).abs().max().item() <= 1e-5 * scale
+        assert (b - f).abs().max().item() <= 1e-5 * scale
+
+
+def test_scene_order_backward_paper_appearance(tiny):
+    """The scene-order backward with the paper's appearance model and the
+    distortion loss equals vt_render_bwd mapped to scene order, both maps."""
+    wl, osc, o, d = tiny
+    sc = wl.scene
+    tvd = np.random.default_rng(25).normal(0, 0.5, size=sc.tex.shape).astype(np.float32)
+    scene = api.Scene(sc.sites, sc.sigma, sc.tex, sc.offsets, sc.indices, tex_vd=tvd)
+    P = gpu_params(wl.params, img_w=64, img_h=64, n_images=1, appearance=1)
+    to, td = to_dev(o, d)
+    res = torch.empty(len(o), 3, device=DEV)
+    dist = torch.empty(len(o), 3, device=DEV)
+    rgb = api.render_fwd(scene, to, td, P, residual=res, dist=dist)[0]
+    g = seeded(len(o), 3, seed=109)
+    gd = seeded(len(o), seed=110, normal=False)
+    vd_ref = torch.empty(sc.n, sc.R, sc.R, 3, device=DEV)
+    ref = api.render_bwd(scene, to, td, P, rgb, g, residual=res, dist=dist, grad_dist=gd, tex_vd_out=vd_ref)
+    gc, gt, gv = api.render_bwd_scene_order(scene, to, td, P, rgb, g, residual=res, dist=dist, grad_dist=gd)
+    got = _scene_order_to_user(scene, gc, gt)
+    perm = scene.permutation().long()
+    vd = torch.empty_like(vd_ref)
+    vd[perm] = gv[..., :3]
+    for a, b in zip(list(got) + [vd], list(ref) + [vd_ref]):
+        assert (a - b).abs().max().item() <= 1e-5 * max(1.0, b.abs().max().item())
+
+
 def test_cuda_path_matches_stored_golden_values():
     """The CUDA path against the stored oracle values of tests/golden (no
     oracle run): cells and step counts exact, colours within 1e-4."""
