@@ -210,10 +210,12 @@ def recorded_traffic(kernel, workload):
     return None
 
 
-def recorded_issue(kernel, workload):
+def recorded_issue(kernel):
     """Issue-slot activity (fraction of cycles a warp instruction issued) of
     the kernel from the committed ncu summaries (lines "ISSUE <kernel>
-    <workload> <fraction> <source hash>"), on the current sources only."""
+    <workload> <fraction> <source hash>", taken on a smaller workload than the
+    benchmark's because the metric needs several ncu passes), on the current
+    sources only: {"value", "workload"} or None."""
     d = os.path.join(ROOT, "profiles")
     try:
         names = sorted(os.listdir(d))
@@ -226,8 +228,8 @@ def recorded_issue(kernel, workload):
         with open(os.path.join(d, n)) as f:
             for line in f:
                 w = line.split()
-                if len(w) == 5 and w[0] == "ISSUE" and w[1] == kernel and w[2] == workload and w[4] == h:
-                    return float(w[3])
+                if len(w) == 5 and w[0] == "ISSUE" and w[1] == kernel and w[4] == h:
+                    return {"value": float(w[3]), "workload": w[2]}
     return None
 
 
@@ -661,7 +663,7 @@ def run_ours(args, ws, rank, local):
     # the walk instantiation: mode, texel storage, appearance model
     kname = f"k_walk<{dom.upper()},{args.tex}" + (",appearance1>" if args.appearance else ">")
     traffic = recorded_traffic(kname, args.workload)
-    issue = recorded_issue(kname, args.workload)
+    issue = recorded_issue(kname)
     # achieved = demand bytes / event-timed kernel; frac against the measured
     # HBM copy peak; the same demand against the L2 read bandwidth measured
     # here; DRAM bytes (ncu) / kernel time against the HBM peak. The kernel is
