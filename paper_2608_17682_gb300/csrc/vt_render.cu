@@ -400,23 +400,39 @@ __device__ int greedy_nearest(const Scene& S, int cell, float3 q, int max_steps,
 
 // ---------------------------------------------------------------- anchors
 // Exact nearest site of each anchor point: packed (distance bits, user id)
-// atomicMin over all sites; blockIdx.y selects the anchor.
-__global__ void k_anchor_nn(Scene S, RP P, const float* __restrict__ o, unsigned long long* key) {
-  int a = blockIdx.y;
-  const int64_t ar = anchor_ray(P, a);
-  float3 q = make_float3(o[3 * ar], o[3 * ar + 1], o[3 * ar + 2]);
-  unsigned long long best = ~0ull;
+// atomicMin over all sites. Each thread reads a site record once for a group
+// of up to kAnchorGroup anchors (blockIdx.y selects the group) and keeps the
+// group's minima in registers; warps reduce them before the atomics.
+constexpr int kAnchorGroup = 16;
+__global__ void k_anchor_nn(Scene S, RP P, const float* __restrict__ o, int n_anchors, unsigned long long* key) {
+  const int a0 = blockIdx.y * kAnchorGroup;
+  const int na = min(kAnchorGroup, n_anchors - a0);
+  float3 q[kAnchorGroup];
+  unsigned long long best[kAnchorGroup];
+#pragma unroll
+  for (int a = 0; a < kAnchorGroup; ++a) {
+    const int64_t ar = anchor_ray(P, a0 + min(a, na - 1));
+    q[a] = make_float3(o[3 * ar], o[3 * ar + 1], o[3 * ar + 2]);
+    best[a] = ~0ull;
+  }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.n; i += (int64_t)gridDim.x * blockDim.x) {
     const float4 s = cell_pos(S.cell, (int)i);
-    const float dd = dist2(q, s.x, s.y, s.z);
-    unsigned long long k = ((unsigned long long)__float_as_uint(dd) << 32) | (unsigned)cell_csr(S.cell, (int)i).z;
-    best = k < best ? k : best;
+    const unsigned uid = (unsigned)cell_csr(S.cell, (int)i).z;
+#pragma unroll
+    for (int a = 0; a < kAnchorGroup; ++a) {
+      const unsigned long long k = ((unsigned long long)__float_as_uint(dist2(q[a], s.x, s.y, s.z)) << 32) | uid;
+      best[a] = k < best[a] ? k : best[a];
+    }
   }
-  for (int off = 16; off > 0; off >>= 1) {
-    unsigned long long v = __shfl_xor_sync(0xffffffffu, best, off);
-    best = v < best ? v : best;
+#pragma unroll
+  for (int a = 0; a < kAnchorGroup; ++a) {
+    unsigned long long b = best[a];
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, b, off);
+      b = v < b ? v : b;
+    }
+    if ((threadIdx.x & 31) == 0 && a < na) atomicMin(key + a0 + a, b);
   }
-  if ((threadIdx.x & 31) == 0) atomicMin(key + a, best);
 }
 
 __global__ void k_anchor_refine(Scene S, RP P, const float* __restrict__ o, int n_anchors,
@@ -1166,9 +1182,9 @@ vt_status anchors(vt_scene* s, const Scene& S, const RP& P, const float* o, cuda
   const int na = n_anchors(P);
   if (na < 1 || na > VT_MAX_ANCHORS) return VT_ERR_INVALID_ARG;
   VT_CUDA_TRY(cudaMemsetAsync(s->anchor_key, 0xff, na * sizeof(unsigned long long), st));
-  dim3 g(vt_grid(s->n, 256, 152 * 2), na);
+  dim3 g(vt_grid(s->n, 256, 152 * 4), (na + kAnchorGroup - 1) / kAnchorGroup);
   vt_note_launch();
-  k_anchor_nn<<<g, 256, 0, st>>>(S, P, o, s->anchor_key);
+  k_anchor_nn<<<g, 256, 0, st>>>(S, P, o, na, s->anchor_key);
   vt_note_launch();
   k_anchor_refine<<<1, 64, 0, st>>>(S, P, o, na, s->inv, s->anchor_key, s->anchor_cell, P.max_steps);
   VT_CUDA_TRY(cudaGetLastError());
