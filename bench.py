@@ -432,6 +432,18 @@ def run_ours(args, ws, rank, local):
                     "ms_bwd": round(m_b, 3), "ms_walk_kernel": {"fwd": round(w_t["fwd"], 4),
                                                                 "bwd": round(w_t["bwd"], 4)}}
         grads_by_dtype[t] = [x.clone() for x in (gs, gsig, gt)]
+    # FP16 against FP32 textures, interleaved: three rounds of both, so that
+    # the comparison carries its run-to-run spread
+    if "f32" in scenes and args.tex != "f32":
+        rounds = {args.tex: [], "f32": []}
+        for _ in range(3):
+            for t in (args.tex, "f32"):
+                rounds[t].append(n_rays / (timed(scenes[t], max(3, args.steps // 2))[0] * 1e-3) / 1e6 * ws)
+        extra["tex_vs_f32_interleaved"] = {
+            t: {"median_mrays_s": round(statistics.median(v), 2), "min": round(min(v), 2), "max": round(max(v), 2)}
+            for t, v in rounds.items()}
+        extra["tex_vs_f32_interleaved"]["median_ratio"] = round(
+            statistics.median(rounds[args.tex]) / statistics.median(rounds["f32"]), 4)
     # gradients of the same L2 step with each texture storage against the FP32 kernel's
     if "f32" in grads_by_dtype and grads_by_dtype["f32"] is not None:
         ref = grads_by_dtype["f32"]
