@@ -88,6 +88,10 @@ constexpr int kNbrUnroll = VT_NBR_UNROLL;
 #define VT_STAGE 0
 #endif
 constexpr int kStageCap = 64;
+// 1: the gradient permute walks the outputs in user order
+#ifndef VT_PERMUTE_USER
+#define VT_PERMUTE_USER 0
+#endif
 
 struct Scene {
   const vt_cell* __restrict__ cell;
@@ -435,18 +439,57 @@ __global__ void k_anchor_nn(Scene S, RP P, const float* __restrict__ o, int n_an
   }
 }
 
+// One warp per anchor: the greedy descent of greedy_nearest with the
+// neighbours of the current cell examined by the 32 lanes at once and the
+// smallest (distance bits, user id) key kept, which is the same order as the
+// sequential scan, so the same cell results.
 __global__ void k_anchor_refine(Scene S, RP P, const float* __restrict__ o, int n_anchors,
                                 const int32_t* __restrict__ inv, const unsigned long long* key, int32_t* cell,
                                 int max_steps) {
-  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = blockIdx.x;
+  const int lane = threadIdx.x & 31;
   if (a >= n_anchors) return;
   const int64_t ar = anchor_ray(P, a);
-  float3 q = make_float3(o[3 * ar], o[3 * ar + 1], o[3 * ar + 2]);
+  const float3 q = make_float3(o[3 * ar], o[3 * ar + 1], o[3 * ar + 2]);
   int c = inv[(int)(key[a] & 0xffffffffu)];
-  bool ok = true;
-  c = greedy_nearest(S, c, q, max_steps, ok);
-  if (!ok) atomicOr(S.err, (unsigned long long)VT_EBIT_MAX_STEPS);
-  cell[a] = c;
+  auto key_of = [&](int j) {
+    const float4 sj = cell_pos(S.cell, j);
+    return ((unsigned long long)__float_as_uint(dist2(q, sj.x, sj.y, sj.z)) << 32) |
+           (unsigned)cell_csr(S.cell, j).z;
+  };
+  unsigned long long kc = key_of(c);
+  bool moved = true;
+  int it = 0;
+  for (; it < max_steps && moved; ++it) {
+    const int4 m = cell_csr(S.cell, c);
+    unsigned long long best = ~0ull;
+    int bj = -1;
+    for (int p = m.x + lane; p < m.y; p += 32) {
+      const int j = __float_as_int(__ldg(&S.nbr[p].w));
+      const unsigned long long kj = key_of(j);
+      if (kj < best) {
+        best = kj;
+        bj = j;
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, off);
+      const int oj = __shfl_xor_sync(0xffffffffu, bj, off);
+      if (ob < best) {
+        best = ob;
+        bj = oj;
+      }
+    }
+    moved = best < kc;  // the same on every lane
+    if (moved) {
+      kc = best;
+      c = bj;
+    }
+  }
+  if (lane == 0) {
+    if (moved) atomicOr(S.err, (unsigned long long)VT_EBIT_MAX_STEPS);
+    cell[a] = c;
+  }
 }
 
 // ---------------------------------------------------------------- ray mapping
@@ -1072,13 +1115,48 @@ __global__ void k_grad_out(int64_t n, int RR, const vt_cell* __restrict__ cells,
   }
 }
 
+// The same permute walking the outputs in user order (cell i = inv[u]): the
+// dense output is written front to back, the touched cells' scratch is read
+// and re-zeroed in scattered 1 KB blocks.
+__global__ void k_grad_out_user(int64_t n, int RR, const int32_t* __restrict__ inv, const float4* __restrict__ g_cell,
+                                float4* g_tex, float* gs, float* gsig, float* gtex, float4* g_tex_vd, float* gtex_vd,
+                                uint8_t* touched) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+    const int64_t i = __ldg(inv + u);
+    const bool hot = !touched || touched[i];
+    if (gtex || touched) copy_tex_grad(lane, RR, hot, g_tex + i * RR, gtex ? gtex + u * RR * 3 : nullptr, touched);
+    if (g_tex_vd && (gtex_vd || touched))
+      copy_tex_grad(lane, RR, hot, g_tex_vd + i * RR, gtex_vd ? gtex_vd + u * RR * 3 : nullptr, touched);
+    if (lane == 0) {
+      if (touched && hot) touched[i] = 0;
+      const float4 c = g_cell[i];
+      if (gs) {
+        gs[3 * u] = c.x;
+        gs[3 * u + 1] = c.y;
+        gs[3 * u + 2] = c.z;
+      }
+      if (gsig) gsig[u] = c.w;
+    }
+  }
+}
+
 // the permute launch (a version whose loops were unrolled for 8x8 textures
 // ran 0.26 ms slower per call on 3M cells and was not kept)
-void launch_grad_out(int64_t n, int RR, const vt_cell* cells, const float4* g_cell, float4* g_tex, float* gs,
-                     float* gsig, float* gtex, float4* g_tex_vd, float* gtex_vd, uint8_t* touched, cudaStream_t st) {
+void launch_grad_out(int64_t n, int RR, const vt_cell* cells, const int32_t* inv, const float4* g_cell, float4* g_tex,
+                     float* gs, float* gsig, float* gtex, float4* g_tex_vd, float* gtex_vd, uint8_t* touched,
+                     cudaStream_t st) {
   vt_note_launch();
+#if VT_PERMUTE_USER
+  (void)cells;
+  k_grad_out_user<<<vt_grid(n * 32, 256, 152 * 16), 256, 0, st>>>(n, RR, inv, g_cell, g_tex, gs, gsig, gtex,
+                                                                   g_tex_vd, gtex_vd, touched);
+#else
+  (void)inv;
   k_grad_out<<<vt_grid(n * 32, 256, 152 * 16), 256, 0, st>>>(n, RR, cells, g_cell, g_tex, gs, gsig, gtex, g_tex_vd,
                                                               gtex_vd, touched);
+#endif
 }
 
 // ---------------------------------------------------------------- host side
@@ -1186,7 +1264,7 @@ vt_status anchors(vt_scene* s, const Scene& S, const RP& P, const float* o, cuda
   vt_note_launch();
   k_anchor_nn<<<g, 256, 0, st>>>(S, P, o, na, s->anchor_key);
   vt_note_launch();
-  k_anchor_refine<<<1, 64, 0, st>>>(S, P, o, na, s->inv, s->anchor_key, s->anchor_cell, P.max_steps);
+  k_anchor_refine<<<na, 32, 0, st>>>(S, P, o, na, s->inv, s->anchor_key, s->anchor_cell, P.max_steps);
   VT_CUDA_TRY(cudaGetLastError());
   return VT_OK;
 }
@@ -1353,7 +1431,7 @@ vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float
   vt_status r = backward_walk(s, n_rays, o, d, p, rgb_out, rgb_residual, dist_out, grad_rgb, grad_dist, st);
   if (r != VT_OK) return r;
   // always launched: it also re-zeroes the flagged cells' texel scratch
-  launch_grad_out(s->n, (int)(s->R * s->R), s->cell, s->g_cell, s->g_tex, grad_sites, grad_sigma, grad_tex,
+  launch_grad_out(s->n, (int)(s->R * s->R), s->cell, s->inv, s->g_cell, s->g_tex, grad_sites, grad_sigma, grad_tex,
                   s->g_tex_vd, grad_tex_vd, s->g_touched, st);
   VT_CUDA_TRY(cudaGetLastError());
   s->g_tex_clean = true;
@@ -1471,8 +1549,8 @@ vt_status vt_render_bwd_static(vt_scene* s, int64_t n_rays, const float* o, cons
     if (r != VT_OK) return r;
   }
   if (grad_sites || grad_sigma || grad_tex) {
-    launch_grad_out(s->n, (int)RR, s->cell, g_cell, g_tex, grad_sites, grad_sigma, grad_tex, nullptr, nullptr,
-                    nullptr, st);
+    launch_grad_out(s->n, (int)RR, s->cell, s->inv, g_cell, g_tex, grad_sites, grad_sigma, grad_tex, nullptr,
+                    nullptr, nullptr, st);
     VT_CUDA_TRY(cudaGetLastError());
   }
   return VT_OK;
