@@ -88,10 +88,6 @@ constexpr int kNbrUnroll = VT_NBR_UNROLL;
 #define VT_STAGE 0
 #endif
 constexpr int kStageCap = 64;
-// 1: the gradient permute walks the outputs in user order
-#ifndef VT_PERMUTE_USER
-#define VT_PERMUTE_USER 0
-#endif
 
 struct Scene {
   const vt_cell* __restrict__ cell;
@@ -1115,48 +1111,14 @@ __global__ void k_grad_out(int64_t n, int RR, const vt_cell* __restrict__ cells,
   }
 }
 
-// The same permute walking the outputs in user order (cell i = inv[u]): the
-// dense output is written front to back, the touched cells' scratch is read
-// and re-zeroed in scattered 1 KB blocks.
-__global__ void k_grad_out_user(int64_t n, int RR, const int32_t* __restrict__ inv, const float4* __restrict__ g_cell,
-                                float4* g_tex, float* gs, float* gsig, float* gtex, float4* g_tex_vd, float* gtex_vd,
-                                uint8_t* touched) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
-    const int64_t i = __ldg(inv + u);
-    const bool hot = !touched || touched[i];
-    if (gtex || touched) copy_tex_grad(lane, RR, hot, g_tex + i * RR, gtex ? gtex + u * RR * 3 : nullptr, touched);
-    if (g_tex_vd && (gtex_vd || touched))
-      copy_tex_grad(lane, RR, hot, g_tex_vd + i * RR, gtex_vd ? gtex_vd + u * RR * 3 : nullptr, touched);
-    if (lane == 0) {
-      if (touched && hot) touched[i] = 0;
-      const float4 c = g_cell[i];
-      if (gs) {
-        gs[3 * u] = c.x;
-        gs[3 * u + 1] = c.y;
-        gs[3 * u + 2] = c.z;
-      }
-      if (gsig) gsig[u] = c.w;
-    }
-  }
-}
-
-// the permute launch (a version whose loops were unrolled for 8x8 textures
-// ran 0.26 ms slower per call on 3M cells and was not kept)
-void launch_grad_out(int64_t n, int RR, const vt_cell* cells, const int32_t* inv, const float4* g_cell, float4* g_tex,
-                     float* gs, float* gsig, float* gtex, float4* g_tex_vd, float* gtex_vd, uint8_t* touched,
-                     cudaStream_t st) {
+// the permute launch (measured alternatives, 3M cells: loops unrolled for 8x8
+// textures, +0.26 ms per call; outputs walked in user order, -0.02 ms, within
+// noise; neither kept)
+void launch_grad_out(int64_t n, int RR, const vt_cell* cells, const float4* g_cell, float4* g_tex, float* gs,
+                     float* gsig, float* gtex, float4* g_tex_vd, float* gtex_vd, uint8_t* touched, cudaStream_t st) {
   vt_note_launch();
-#if VT_PERMUTE_USER
-  (void)cells;
-  k_grad_out_user<<<vt_grid(n * 32, 256, 152 * 16), 256, 0, st>>>(n, RR, inv, g_cell, g_tex, gs, gsig, gtex,
-                                                                   g_tex_vd, gtex_vd, touched);
-#else
-  (void)inv;
   k_grad_out<<<vt_grid(n * 32, 256, 152 * 16), 256, 0, st>>>(n, RR, cells, g_cell, g_tex, gs, gsig, gtex, g_tex_vd,
                                                               gtex_vd, touched);
-#endif
 }
 
 // ---------------------------------------------------------------- host side
@@ -1431,7 +1393,7 @@ vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float
   vt_status r = backward_walk(s, n_rays, o, d, p, rgb_out, rgb_residual, dist_out, grad_rgb, grad_dist, st);
   if (r != VT_OK) return r;
   // always launched: it also re-zeroes the flagged cells' texel scratch
-  launch_grad_out(s->n, (int)(s->R * s->R), s->cell, s->inv, s->g_cell, s->g_tex, grad_sites, grad_sigma, grad_tex,
+  launch_grad_out(s->n, (int)(s->R * s->R), s->cell, s->g_cell, s->g_tex, grad_sites, grad_sigma, grad_tex,
                   s->g_tex_vd, grad_tex_vd, s->g_touched, st);
   VT_CUDA_TRY(cudaGetLastError());
   s->g_tex_clean = true;
@@ -1549,8 +1511,8 @@ vt_status vt_render_bwd_static(vt_scene* s, int64_t n_rays, const float* o, cons
     if (r != VT_OK) return r;
   }
   if (grad_sites || grad_sigma || grad_tex) {
-    launch_grad_out(s->n, (int)RR, s->cell, s->inv, g_cell, g_tex, grad_sites, grad_sigma, grad_tex, nullptr,
-                    nullptr, nullptr, st);
+    launch_grad_out(s->n, (int)RR, s->cell, g_cell, g_tex, grad_sites, grad_sigma, grad_tex, nullptr, nullptr,
+                    nullptr, st);
     VT_CUDA_TRY(cudaGetLastError());
   }
   return VT_OK;
