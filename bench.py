@@ -180,10 +180,12 @@ def _code_only(text):
 
 
 def kernel_source_hash():
-    """Hash of the CUDA sources' code (comments and spacing ignored)."""
+    """Hash of the code (comments and spacing ignored) of the translation
+    unit that holds the walk kernels and the gradient permute, and of its
+    internal header: the sources the recorded ncu figures depend on."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2608_17682_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in ("vt_internal.cuh", "vt_render.cu"):
         with open(os.path.join(d, f), encoding="utf-8") as fh:
             h.update(f.encode() + _code_only(fh.read()).encode())
     return h.hexdigest()[:16]
