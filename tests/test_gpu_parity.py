@@ -355,6 +355,50 @@ def test_empty_and_missing_rays(tiny):
         assert gs.abs().max().item() == 0 and gsig.abs().max().item() == 0 and gt.abs().max().item() == 0
 
 
+def test_grazing_planes_take_the_fp64_recheck(tiny):
+    """Rays nearly parallel to a bisector plane of the cell they start near
+    (|n.d| from 1e-8 to 9e-7 of |n||d|, origins 1e-5 to 1e-4 off the plane):
+    their exit decisions go through the FP64 recheck of grazing planes (the
+    library counts the rechecks), and cells, steps and colours still match
+    the oracle outside the degenerate band."""
+    wl, osc, o_, d_ = tiny
+    sc = wl.scene
+    rng = np.random.default_rng(31)
+    os_, ds = [], []
+    for _ in range(3000):
+        i = int(rng.integers(sc.n))
+        nb = sc.indices[sc.offsets[i]:sc.offsets[i + 1]]
+        j = int(rng.choice(nb))
+        si, sj = sc.sites[i].astype(np.float64), sc.sites[j].astype(np.float64)
+        nh = (sj - si) / np.linalg.norm(sj - si)
+        t1 = np.cross(nh, rng.normal(size=3))
+        t1 /= np.linalg.norm(t1)
+        h = rng.choice([1e-5, 3e-5, 1e-4])
+        eps = rng.choice([1e-8, 3e-7, 9e-7])
+        os_.append(0.5 * (si + sj) - h * nh - 0.02 * t1)
+        d = t1 + eps * nh
+        ds.append(d / np.linalg.norm(d))
+    o = np.asarray(os_, np.float32)
+    d = np.asarray(ds, np.float32)
+    scene = api.Scene.from_workload(sc)
+    P = gpu_params(wl.params)
+    to, td = to_dev(o, d)
+    rgb, T, steps = api.render_fwd(scene, to, td, P)
+    cells, _, n_cells = api.trace_cells(scene, to, td, P, max_cells=256)
+    st, n_fp64 = scene.get_error()
+    assert st == 0 and n_fp64 > 0
+    op = oracle_params(wl.params)
+    orgb, oT, osteps, flags = O.render(osc, o, d, params=op)
+    oc, _, on, _ = O.trace(osc, o, d, max_cells=256, params=op)
+    ok = (flags & O.BAND_FLAGS) == 0
+    assert ok.mean() > 0.5
+    compare_sequences(cells.cpu().numpy(), n_cells.cpu().numpy(), oc, on, flags, name="grazing rays")
+    image_report("grazing rays image", rgb.cpu().numpy(), orgb, flags)
+    assert np.array_equal(steps.cpu().numpy()[ok], osteps[ok])
+    assert np.abs(rgb.cpu().numpy()[ok] - orgb[ok]).max() <= IMG_TOL
+    parity_log.record("grazing rays FP64 rechecks", rechecks=int(n_fp64))
+
+
 def test_single_site_scene_closed_form():
     c = np.array([0.2, 0.5, 0.9], np.float32)
     tex = np.broadcast_to(c, (1, 4, 4, 3)).copy()
