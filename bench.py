@@ -659,34 +659,56 @@ def run_ours(args, ws, rank, local):
     except RuntimeError as e:  # report, do not fail the benchmark line
         extra["cuda_graph_step"] = {"error": str(e).splitlines()[0][:200]}
 
-    # end to end through the public API with host buffers: H2D target image,
-    # D2H rendered image + loss, inside the timed region
+    # end to end through the public API with host buffers: every step copies
+    # its target image from pinned host memory to the device and reads the
+    # rendered image and the loss back, inside the timed region. The copies
+    # run on a second stream: the image read-back overlaps the step's
+    # backward and the next step's target upload overlaps this step, so the
+    # copy engines work beside the kernels (the first upload and the last
+    # read-back are inside the timed events too).
     Yh = torch.as_tensor(W.target_image(n_rays, wl.seed)).pin_memory()
     rgb_h = torch.empty(n_rays, 3).pin_memory()
     loss_h = torch.empty(1).pin_memory()
-    Yd = torch.empty_like(Y)
+    Yd = [torch.empty_like(Y) for _ in range(2)]
+    copy = torch.cuda.Stream()
+    y_ready = [torch.cuda.Event() for _ in range(2)]
+    fwd_done, d2h_done = torch.cuda.Event(), torch.cuda.Event()
 
-    def e2e_step():
-        Yd.copy_(Yh, non_blocking=True)
-        api.generate_rays(cams, out=(o, d, tm))
-        api.render_fwd(main, o, d, params, time=tm, out=(rgb, T, steps), residual=res)
-        loss, grad = api.l2_loss(rgb, Yd)
-        api.render_bwd(main, o, d, params, rgb, grad, time=tm, out=(gs, gsig, gt), residual=res)
-        rgb_h.copy_(rgb, non_blocking=True)
-        loss_h.copy_(loss, non_blocking=True)
+    def e2e_run(n_steps):
+        copy.wait_stream(stream)
+        with torch.cuda.stream(copy):
+            Yd[0].copy_(Yh, non_blocking=True)
+            y_ready[0].record(copy)
+        for k in range(n_steps):
+            if k > 0:
+                stream.wait_event(d2h_done)  # the previous image is on the host before rgb is rewritten
+            api.generate_rays(cams, out=(o, d, tm))
+            api.render_fwd(main, o, d, params, time=tm, out=(rgb, T, steps), residual=res)
+            fwd_done.record(stream)
+            with torch.cuda.stream(copy):
+                copy.wait_event(fwd_done)
+                rgb_h.copy_(rgb, non_blocking=True)
+                d2h_done.record(copy)
+                if k + 1 < n_steps:
+                    Yd[(k + 1) % 2].copy_(Yh, non_blocking=True)
+                    y_ready[(k + 1) % 2].record(copy)
+            stream.wait_event(y_ready[k % 2])
+            loss, grad = api.l2_loss(rgb, Yd[k % 2])
+            loss_h.copy_(loss, non_blocking=True)
+            api.render_bwd(main, o, d, params, rgb, grad, time=tm, out=(gs, gsig, gt), residual=res)
+        stream.wait_event(d2h_done)
 
-    for _ in range(args.warmup):
-        e2e_step()
+    e2e_run(args.warmup)
     barrier()
     a, b = ev(), ev()
     a.record(stream)
-    for _ in range(args.steps):
-        e2e_step()
+    e2e_run(args.steps)
     b.record(stream)
     barrier()
     ms_e2e = a.elapsed_time(b) / args.steps
     e2e = {"value": round(total_rays / (ms_e2e * 1e-3) / 1e6, 3), "unit": "Mrays/s",
-           "h2d_bytes_per_step": int(Yh.numel() * 4), "d2h_bytes_per_step": int(rgb_h.numel() * 4 + 4)}
+           "h2d_bytes_per_step": int(Yh.numel() * 4), "d2h_bytes_per_step": int(rgb_h.numel() * 4 + 4),
+           "copies": "on a second stream, overlapped with the kernels"}
 
     # roofline of the dominant kernel: algorithmic (demand) bytes per visited
     # cell, the byte model of the scope table: cell record, neighbour records,
