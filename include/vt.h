@@ -292,7 +292,10 @@ vt_status vt_render_bwd(vt_scene* s, int64_t n_rays, const float* o, const float
  * where cell k is the user's site vt_scene_permutation()[k]. They hold this
  * call's gradients until the next backward call on the scene (of either
  * kind) or its destruction; the next call re-zeroes only the texel blocks
- * this one wrote. Read them on `stream` (or after synchronising it). */
+ * this one wrote. Read them on `stream` (or after synchronising it).
+ * grad_cell and grad_tex must not be NULL (VT_ERR_INVALID_ARG); the other
+ * errors are those of vt_render_bwd. On any error the three pointers are set
+ * to NULL (grad_tex_vd only if it was given). */
 vt_status vt_render_bwd_scene_order(vt_scene* s, int64_t n_rays, const float* o, const float* d, const float* time,
                                     const vt_render_params* p, const float* rgb_out, const float* rgb_residual,
                                     const float* dist_out, const float* grad_rgb, const float* grad_dist,
