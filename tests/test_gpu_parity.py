@@ -916,8 +916,8 @@ def test_half_offsets_forward_against_exact_walk(medium):
     frac = same[ok].mean()
     rmse_h = float(np.sqrt(np.mean((rgb_h - orgb) ** 2)))
     rmse_f = float(np.sqrt(np.mean((rgb_f[ok] - orgb[ok]) ** 2)))
-    print(f"half offsets: {int((~same & ok).sum())} / {int(ok.sum())} unflagged sequences differ; "
-          f"image RMSE {rmse_h:.3g} (exact offsets {rmse_f:.3g})")
+    parity_log.record("50k-site FP16 neighbour offsets (not exact by design)", rays=len(o),
+                      unflagged_seq_differ=int((~same & ok).sum()), rmse=rmse_h, rmse_exact_offsets=rmse_f)
     assert frac >= 0.9 and rmse_h <= 5e-3
     # forward only
     with pytest.raises(api.VTError):
