@@ -563,7 +563,8 @@ def run_ours(args, ws, rank, local):
         extra["train_iteration"] = {"rays_per_iter": tr.B, "ms_per_iter": round(ms_it, 3),
                                     "mrays_s": round(tr.B / (ms_it * 1e-3) / 1e6, 2), "kernel_status": st_,
                                     "note": "sigma=exp(rho), sampling, fwd+bwd (appearance 1, distortion), "
-                                            "Smooth-L1, regularisers, 4 Adam updates; L2 not flushed"}
+                                            "Smooth-L1, gradients left in scene order and consumed by fused Adam "
+                                            "steps (regularisers and Eq. 4 inside); L2 not flushed"}
         tr.scene.close()
         del tr
 

@@ -409,6 +409,36 @@ uint64_t vt_kernel_launches(void);
  * pointer, size or count. */
 vt_status vt_stream_read(const void* buf, int64_t bytes, int32_t reps, float* sink, void* stream);
 
+/* Adam steps that take the gradients of vt_render_bwd_scene_order directly
+ * (scene cell order, float4 records) and update user-order parameters, so a
+ * training step needs no user-order gradient arrays. perm [N] is
+ * vt_scene_permutation (scene cell k = user cell perm[k]); Adam as in
+ * vt_adam_step (bias correction at `step`); all pointers DEVICE, FP32.
+ *
+ * Texture map: grad_tex_scene [N][R][R][4] (RGBA, A ignored); tex, m, v
+ * [N][R][R][3] user order, updated in place. The map's regulariser of Eq. 5
+ * is fused in: regularizer 0 adds lambda * L_mean (for T_vi), 1 adds lambda *
+ * L_vd (for T_vd), both normalised by N R^2 as in vt_texture_regularizers;
+ * its gradient is taken at the parameters before the update and its loss is
+ * ADDED to *loss_out (one float; NULL allowed when lambda == 0). With lr == 0
+ * the parameters and moments are left as they are and only the loss is
+ * added. VT_ERR_INVALID_ARG on a bad size, regulariser id, Adam constant or a
+ * missing pointer. */
+vt_status vt_adam_step_tex_scene_order(int64_t n_cells, int32_t tex_res, const int32_t* perm,
+                                      const float* grad_tex_scene, float* tex, float* m, float* v, int32_t regularizer,
+                                      float lambda, float lr, float beta1, float beta2, float eps, int64_t step,
+                                      float* loss_out, void* stream);
+
+/* Sites and log-densities: grad_cell_scene [N][4] = {dL/ds, dL/dsigma} in
+ * scene order; sites [N,3], rho [N] (sigma = exp(rho), Sec. 5.4) and their
+ * moments in user order; sigma [N] user order, the densities the gradients
+ * were taken at. dL/drho = dL/dsigma * sigma (Eq. 4). A rate of 0 skips that
+ * parameter (its pointers may then be NULL). */
+vt_status vt_adam_step_cells_scene_order(int64_t n_cells, const int32_t* perm, const float* grad_cell_scene,
+                                        float* sites, float* rho, const float* sigma, float* m_sites, float* v_sites,
+                                        float* m_rho, float* v_rho, float lr_sites, float lr_rho, float beta1,
+                                        float beta2, float eps, int64_t step, void* stream);
+
 /* Human-readable status name (static string). */
 const char* vt_status_str(vt_status s);
 

@@ -23,7 +23,7 @@ EXPORTS = ["vt_render_params_default", "vt_scene_create", "vt_scene_update", "vt
            "vt_scene_get_error", "vt_camera_n_rays", "vt_generate_rays", "vt_render_fwd", "vt_render_bwd",
            "vt_render_bwd_static", "vt_render_bwd_scene_order", "vt_scene_permutation", "vt_trace_cells", "vt_l2_loss", "vt_average_samples", "vt_average_samples_bwd", "vt_sigma_from_rho",
            "vt_sigma_from_rho_bwd", "vt_sample_rays", "vt_smooth_l1_loss", "vt_texture_regularizers", "vt_adam_step",
-           "vt_kernel_launches", "vt_stream_read", "vt_status_str"]
+           "vt_adam_step_tex_scene_order", "vt_adam_step_cells_scene_order", "vt_kernel_launches", "vt_stream_read", "vt_status_str"]
 
 
 class VTError(RuntimeError):
@@ -87,6 +87,10 @@ def _load():
         "vt_smooth_l1_loss": ([I64, P, P, C.c_float, P, P, P], C.c_int),
         "vt_texture_regularizers": ([I64, I32, P, P, C.c_float, C.c_float, P, P, P, P], C.c_int),
         "vt_adam_step": ([I64, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, I64, P], C.c_int),
+        "vt_adam_step_tex_scene_order": ([I64, I32, P, P, P, P, P, I32, C.c_float, C.c_float, C.c_float, C.c_float,
+                                          C.c_float, I64, P, P], C.c_int),
+        "vt_adam_step_cells_scene_order": ([I64, P, P, P, P, P, P, P, P, P, C.c_float, C.c_float, C.c_float,
+                                            C.c_float, C.c_float, I64, P], C.c_int),
         "vt_kernel_launches": ([], C.c_uint64),
         "vt_stream_read": ([P, I64, I32, P, P], C.c_int),
         "vt_status_str": ([C.c_int], C.c_char_p),
@@ -264,3 +268,23 @@ def vt_kernel_launches() -> int:
 
 def vt_stream_read(buf: int, nbytes: int, reps: int, sink: int, stream: int):
     check(lib.vt_stream_read(C.c_void_p(buf), nbytes, reps, C.c_void_p(sink), C.c_void_p(stream)), "vt_stream_read")
+
+
+def vt_adam_step_tex_scene_order(n_cells: int, tex_res: int, perm: int, grad_tex_scene: int, tex: int, m: int, v: int,
+                                 regularizer: int, lam: float, lr: float, beta1: float, beta2: float, eps: float,
+                                 step: int, loss: int, stream: int):
+    check(lib.vt_adam_step_tex_scene_order(n_cells, tex_res, C.c_void_p(perm), C.c_void_p(grad_tex_scene),
+                                           C.c_void_p(tex), C.c_void_p(m), C.c_void_p(v), regularizer, lam, lr, beta1,
+                                           beta2, eps, step, C.c_void_p(loss), C.c_void_p(stream)),
+          "vt_adam_step_tex_scene_order")
+
+
+def vt_adam_step_cells_scene_order(n_cells: int, perm: int, grad_cell_scene: int, sites: int, rho: int, sigma: int,
+                                   m_sites: int, v_sites: int, m_rho: int, v_rho: int, lr_sites: float, lr_rho: float,
+                                   beta1: float, beta2: float, eps: float, step: int, stream: int):
+    check(lib.vt_adam_step_cells_scene_order(n_cells, C.c_void_p(perm), C.c_void_p(grad_cell_scene),
+                                             C.c_void_p(sites), C.c_void_p(rho), C.c_void_p(sigma),
+                                             C.c_void_p(m_sites), C.c_void_p(v_sites), C.c_void_p(m_rho),
+                                             C.c_void_p(v_rho), lr_sites, lr_rho, beta1, beta2, eps, step,
+                                             C.c_void_p(stream)),
+          "vt_adam_step_cells_scene_order")

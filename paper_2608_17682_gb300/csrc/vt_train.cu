@@ -134,6 +134,101 @@ __global__ void k_adam(int64_t n, float* __restrict__ p, const float* __restrict
   }
 }
 
+// Adam on a user-order texture map from scene-order gradients, with the
+// map's regulariser of Eq. 5 fused in. One warp per scene cell k (user cell
+// u = perm[k]): the warp reads the cell's R^2 x 3 parameters, forms the
+// regulariser gradient from them (reg 0: L_mean = 1/(N R^2) sum |T_u -
+// mean_v T_v|^2; reg 1: L_vd = 1/(N R^2) sum |T|^2), adds the RGB part of the
+// scene-order RGBA render gradient, and updates parameter and moments in place
+// (no update when lr == 0; the regulariser's loss is still added to *loss).
+__global__ void k_adam_tex_scene(int64_t n, int RR, const int32_t* __restrict__ perm,
+                                 const float4* __restrict__ gsc, float* __restrict__ tex, float* __restrict__ m,
+                                 float* __restrict__ v, int reg, float lam, float lr, float b1, float b2, float eps,
+                                 float c1, float c2, float* loss) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float scale = 1.f / ((float)n * (float)RR);
+  double acc = 0.0;
+  for (int64_t k = warp0; k < n; k += warps) {
+    const int64_t base = (int64_t)perm[k] * RR * 3;
+    float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+    if (reg == 0 && lam != 0.f) {
+      for (int t = lane; t < RR; t += 32) {
+        m0 += tex[base + 3 * t];
+        m1 += tex[base + 3 * t + 1];
+        m2 += tex[base + 3 * t + 2];
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        m0 += __shfl_xor_sync(0xffffffffu, m0, off);
+        m1 += __shfl_xor_sync(0xffffffffu, m1, off);
+        m2 += __shfl_xor_sync(0xffffffffu, m2, off);
+      }
+      m0 /= (float)RR;
+      m1 /= (float)RR;
+      m2 /= (float)RR;
+    }
+    for (int e = lane; e < RR * 3; e += 32) {
+      const int t = e / 3, c = e - 3 * t;
+      const float p = tex[base + e];
+      float rg = 0.f;
+      if (lam != 0.f) {
+        const float r = reg == 0 ? p - (c == 0 ? m0 : (c == 1 ? m1 : m2)) : p;
+        acc += (double)lam * scale * r * r;
+        rg = 2.f * lam * scale * r;
+      }
+      if (lr != 0.f) {
+        const float4 gq = gsc[k * RR + t];
+        const float gi = (c == 0 ? gq.x : (c == 1 ? gq.y : gq.z)) + rg;
+        const float mi = b1 * m[base + e] + (1.f - b1) * gi;
+        const float vi = b2 * v[base + e] + (1.f - b2) * gi * gi;
+        m[base + e] = mi;
+        v[base + e] = vi;
+        tex[base + e] = p - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+      }
+    }
+  }
+  const double t = block_sum(acc);
+  if (threadIdx.x == 0 && loss) atomicAdd(loss, (float)t);
+}
+
+// Adam on user-order sites and log-densities from the scene-order cell
+// gradients {dL/ds, dL/dsigma}: dL/drho = dL/dsigma * sigma (Eq. 4).
+__global__ void k_adam_cells_scene(int64_t n, const int32_t* __restrict__ perm, const float4* __restrict__ gc,
+                                   float* __restrict__ sites, float* __restrict__ rho, const float* __restrict__ sigma,
+                                   float* __restrict__ ms, float* __restrict__ vs, float* __restrict__ mr,
+                                   float* __restrict__ vr, float lr_s, float lr_r, float b1, float b2, float eps,
+                                   float c1, float c2) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u = perm[k];
+    const float4 g = gc[k];
+    if (lr_s != 0.f) {
+      const float gs[3] = {g.x, g.y, g.z};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int64_t e = 3 * u + a;
+        const float mi = b1 * ms[e] + (1.f - b1) * gs[a];
+        const float vi = b2 * vs[e] + (1.f - b2) * gs[a] * gs[a];
+        ms[e] = mi;
+        vs[e] = vi;
+        sites[e] -= lr_s * (mi / c1) / (sqrtf(vi / c2) + eps);
+      }
+    }
+    if (lr_r != 0.f) {
+      const float gi = g.w * sigma[u];
+      const float mi = b1 * mr[u] + (1.f - b1) * gi;
+      const float vi = b2 * vr[u] + (1.f - b2) * gi * gi;
+      mr[u] = mi;
+      vr[u] = vi;
+      rho[u] -= lr_r * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+  }
+}
+
+bool adam_args_ok(float beta1, float beta2, float eps, int64_t step) {
+  return step >= 1 && beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps >= 0.f;
+}
+
 }  // namespace
 
 extern "C" {
@@ -188,6 +283,44 @@ vt_status vt_adam_step(int64_t n, float* param, const float* grad, float* m, flo
   vt_note_launch();
   k_adam<<<vt_grid(n, 256, 152 * 16), 256, 0, (cudaStream_t)stream>>>(n, param, grad, m, v, lr, beta1, beta2, eps,
                                                                        c1, c2);
+  VT_CUDA_TRY(cudaGetLastError());
+  return VT_OK;
+}
+
+vt_status vt_adam_step_tex_scene_order(int64_t n_cells, int32_t tex_res, const int32_t* perm,
+                                      const float* grad_tex_scene, float* tex, float* m, float* v, int32_t regularizer,
+                                      float lambda, float lr, float beta1, float beta2, float eps, int64_t step,
+                                      float* loss_out, void* stream) {
+  if (n_cells < 0 || tex_res < 1 || (regularizer != 0 && regularizer != 1)) return VT_ERR_INVALID_ARG;
+  if (!adam_args_ok(beta1, beta2, eps, step)) return VT_ERR_INVALID_ARG;
+  if (n_cells > 0 && (!perm || !tex || (lr != 0.f && (!grad_tex_scene || !m || !v)) || (lambda != 0.f && !loss_out)))
+    return VT_ERR_INVALID_ARG;
+  if (n_cells == 0) return VT_OK;
+  const float c1 = (float)(1.0 - pow((double)beta1, (double)step));
+  const float c2 = (float)(1.0 - pow((double)beta2, (double)step));
+  vt_note_launch();
+  k_adam_tex_scene<<<vt_grid(n_cells * 32, 256, 152 * 8), 256, 0, (cudaStream_t)stream>>>(
+      n_cells, tex_res * tex_res, perm, reinterpret_cast<const float4*>(grad_tex_scene), tex, m, v, regularizer, lambda,
+      lr, beta1, beta2, eps, c1, c2, loss_out);
+  VT_CUDA_TRY(cudaGetLastError());
+  return VT_OK;
+}
+
+vt_status vt_adam_step_cells_scene_order(int64_t n_cells, const int32_t* perm, const float* grad_cell_scene,
+                                        float* sites, float* rho, const float* sigma, float* m_sites, float* v_sites,
+                                        float* m_rho, float* v_rho, float lr_sites, float lr_rho, float beta1,
+                                        float beta2, float eps, int64_t step, void* stream) {
+  if (n_cells < 0 || !adam_args_ok(beta1, beta2, eps, step)) return VT_ERR_INVALID_ARG;
+  if (n_cells > 0 && (!perm || !grad_cell_scene || (lr_sites != 0.f && (!sites || !m_sites || !v_sites)) ||
+                      (lr_rho != 0.f && (!rho || !sigma || !m_rho || !v_rho))))
+    return VT_ERR_INVALID_ARG;
+  if (n_cells == 0) return VT_OK;
+  const float c1 = (float)(1.0 - pow((double)beta1, (double)step));
+  const float c2 = (float)(1.0 - pow((double)beta2, (double)step));
+  vt_note_launch();
+  k_adam_cells_scene<<<vt_grid(n_cells, 256, 152 * 16), 256, 0, (cudaStream_t)stream>>>(
+      n_cells, perm, reinterpret_cast<const float4*>(grad_cell_scene), sites, rho, sigma, m_sites, v_sites, m_rho,
+      v_rho, lr_sites, lr_rho, beta1, beta2, eps, c1, c2);
   VT_CUDA_TRY(cudaGetLastError());
   return VT_OK;
 }

@@ -10,8 +10,11 @@ Each iteration:
   of the view-dependent rate), and a Delaunay refresh every `refresh_every`
   iterations because the sites move (the appendix's periodic update).
 
-Every array operation of the step runs in libvt kernels; torch holds the
-tensors. The Delaunay refresh runs on the host (scipy), outside the kernels.
+Every array operation of the step runs in libvt kernels (apart from zeroing
+the regulariser's loss scalar); torch holds the tensors. By default the
+backward leaves the gradients in the scene's cell order and fused Adam steps
+consume them (no user-order gradient arrays). The Delaunay refresh runs on the
+host (scipy), outside the kernels.
 """
 from __future__ import annotations
 
@@ -44,6 +47,10 @@ class TrainConfig:
     smooth_l1_beta: float = 1e-2
     refresh_every: int = 500
     seed: int = 0
+    # gradients left in the scene's cell order and consumed by fused Adam
+    # steps (regularisers and Eq. 4 included); False: user-order gradients,
+    # then separate regulariser, density-chain and Adam kernels
+    scene_order_grads: bool = True
 
 
 def cosine(lr0, lr1, t):
@@ -102,9 +109,11 @@ class Trainer:
         self.reg = torch.empty(1, device=self.dev)
         n, R = self.p["tex"].shape[0], self.p["tex"].shape[1]
         self.R = R
-        self.g = {"sites": torch.empty(n, 3, device=self.dev), "rho": torch.empty(n, device=self.dev),
-                  "tex": torch.empty(n, R, R, 3, device=self.dev), "tex_vd": torch.empty(n, R, R, 3, device=self.dev)}
-        self.gsig = torch.empty(n, device=self.dev)
+        if not cfg.scene_order_grads:  # user-order gradient arrays of the unfused path
+            self.g = {"sites": torch.empty(n, 3, device=self.dev), "rho": torch.empty(n, device=self.dev),
+                      "tex": torch.empty(n, R, R, 3, device=self.dev),
+                      "tex_vd": torch.empty(n, R, R, 3, device=self.dev)}
+            self.gsig = torch.empty(n, device=self.dev)
         self.it = 0
         self.refreshes = 0
         self.scene = None
@@ -118,6 +127,7 @@ class Trainer:
             self.scene.close()
         self.scene = api.Scene(self.p["sites"], self.sigma, self.p["tex"], offsets, indices, tex_dtype="f32",
                                device=self.dev, tex_vd=self.p["tex_vd"])
+        self.perm = self.scene.permutation()  # scene cell k = user cell perm[k]
         self.n_edges = len(indices)
 
     def refresh(self):
@@ -141,6 +151,11 @@ class Trainer:
                        dist=self.dist)
         s.vt_smooth_l1_loss(self.B, self.rgb.data_ptr(), self.y.data_ptr(), cfg.smooth_l1_beta,
                             self.grad_rgb.data_ptr(), self.loss.data_ptr(), st)
+        if cfg.scene_order_grads:
+            self._fused_update(st)
+            if sync_loss:
+                return self.loss.item(), self.reg.item(), self.dist[:, 0].mean().item()
+            return None
         api.render_bwd(self.scene, self.o, self.d, self.rparams, self.rgb, self.grad_rgb,
                        out=(self.g["sites"], self.gsig, self.g["tex"]), residual=self.res, dist=self.dist,
                        grad_dist=self.gdist, tex_vd_out=self.g["tex_vd"])
@@ -159,6 +174,27 @@ class Trainer:
         if sync_loss:
             return self.loss.item(), self.reg.item(), self.dist[:, 0].mean().item()
         return None
+
+    def _fused_update(self, st):
+        """Backward with the gradients left in scene order, then one fused Adam
+        step per texture map (with its regulariser) and one for sites and
+        densities (with Eq. 4): no user-order gradient arrays are written."""
+        cfg, s = self.cfg, _vt
+        gc, gt, gv = api.render_bwd_scene_order(self.scene, self.o, self.d, self.rparams, self.rgb, self.grad_rgb,
+                                                residual=self.res, dist=self.dist, grad_dist=self.gdist)
+        lrs = learning_rates(cfg, self.it)
+        self.it += 1
+        n = self.p["tex"].shape[0]
+        self.reg.zero_()  # the two texture steps add their regulariser losses
+        for k, g, reg, lam in (("tex", gt, 0, cfg.lambda_mean), ("tex_vd", gv, 1, cfg.lambda_vd)):
+            s.vt_adam_step_tex_scene_order(n, self.R, self.perm.data_ptr(), g.data_ptr(), self.p[k].data_ptr(),
+                                           self.m[k].data_ptr(), self.v[k].data_ptr(), reg, lam, lrs[k], cfg.beta1,
+                                           cfg.beta2, cfg.eps, self.it, self.reg.data_ptr(), st)
+        s.vt_adam_step_cells_scene_order(n, self.perm.data_ptr(), gc.data_ptr(), self.p["sites"].data_ptr(),
+                                         self.p["rho"].data_ptr(), self.sigma.data_ptr(), self.m["sites"].data_ptr(),
+                                         self.v["sites"].data_ptr(), self.m["rho"].data_ptr(),
+                                         self.v["rho"].data_ptr(), lrs["sites"], lrs["rho"], cfg.beta1, cfg.beta2,
+                                         cfg.eps, self.it, st)
 
     def render(self, cams):
         """Render full images of `cams` with the current parameters."""

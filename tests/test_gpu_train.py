@@ -104,3 +104,88 @@ def test_training_reduces_loss_with_delaunay_refresh():
     assert np.mean(losses[-10:]) < 0.5 * np.mean(losses[:10]), (losses[:10], losses[-10:])
     assert m1 < 0.5 * m0, (m0, m1)
     assert torch.isfinite(tr.p["sites"]).all() and torch.isfinite(tr.p["rho"]).all()
+
+
+@pytest.mark.parametrize("reg", [0, 1])
+def test_scene_order_texture_adam_matches_definition(reg):
+    """vt_adam_step_tex_scene_order: scene-order RGBA gradients mapped to user
+    order through the permutation, the regulariser of Eq. 5 (L_mean or L_vd)
+    added at the parameters before the step, then Adam — against the float64
+    definitions; two steps, the second with another gradient."""
+    rng = np.random.default_rng(44 + reg)
+    n, R = 2003, 4
+    perm = rng.permutation(n).astype(np.int32)
+    p = rng.normal(size=(n, R, R, 3)).astype(np.float32)
+    tp = torch.as_tensor(p, device=DEV).clone()
+    tm, tv = torch.zeros_like(tp), torch.zeros_like(tp)
+    rp, rm, rv = p.astype(np.float64), np.zeros(p.shape), np.zeros(p.shape)
+    tperm = torch.as_tensor(perm, device=DEV)
+    lam, lr = 0.3, 1e-2
+    for k in range(1, 3):
+        gsc = rng.normal(size=(n, R, R, 4)).astype(np.float32)
+        loss = torch.zeros(1, device=DEV)
+        _vt.vt_adam_step_tex_scene_order(n, R, tperm.data_ptr(), torch.as_tensor(gsc, device=DEV).data_ptr(),
+                                         tp.data_ptr(), tm.data_ptr(), tv.data_ptr(), reg, lam, lr, 0.9, 0.999, 1e-15, k,
+                                         loss.data_ptr(), _st())
+        g_user = np.empty(p.shape)
+        g_user[perm] = gsc[..., :3]
+        if reg == 0:
+            L, g_reg, _ = TR.texture_regularizers(rp, np.zeros(p.shape), 0.0, lam)
+        else:
+            L, _, g_reg = TR.texture_regularizers(np.zeros(p.shape), rp, lam, 0.0)
+        assert abs(loss.item() - L) <= 1e-5 * L
+        rp, rm, rv = TR.adam(rp, g_user + g_reg, rm, rv, lr, 0.9, 0.999, 1e-15, k)
+        assert np.abs(tp.cpu().numpy() - rp).max() <= 2e-6, k
+
+
+def test_scene_order_cell_adam_matches_definition():
+    """vt_adam_step_cells_scene_order: site gradients and dL/drho =
+    dL/dsigma * sigma (Eq. 4) from scene-order records, Adam in user order."""
+    rng = np.random.default_rng(46)
+    n = 5001
+    perm = rng.permutation(n).astype(np.int32)
+    sites = rng.normal(size=(n, 3)).astype(np.float32)
+    rho = rng.normal(size=n).astype(np.float32)
+    sigma = np.exp(rho).astype(np.float32)
+    gc = rng.normal(size=(n, 4)).astype(np.float32)
+    ts, tr_ = torch.as_tensor(sites, device=DEV).clone(), torch.as_tensor(rho, device=DEV).clone()
+    z = [torch.zeros(n, 3, device=DEV), torch.zeros(n, 3, device=DEV), torch.zeros(n, device=DEV),
+         torch.zeros(n, device=DEV)]
+    _vt.vt_adam_step_cells_scene_order(n, torch.as_tensor(perm, device=DEV).data_ptr(),
+                                       torch.as_tensor(gc, device=DEV).data_ptr(), ts.data_ptr(), tr_.data_ptr(),
+                                       torch.as_tensor(sigma, device=DEV).data_ptr(), *[x.data_ptr() for x in z],
+                                       2e-3, 5e-2, 0.9, 0.999, 1e-15, 1, _st())
+    gs_u = np.empty((n, 3))
+    gs_u[perm] = gc[:, :3]
+    gr_u = np.empty(n)
+    gr_u[perm] = gc[:, 3] * sigma[perm]
+    rs = TR.adam(sites, gs_u, np.zeros((n, 3)), np.zeros((n, 3)), 2e-3, 0.9, 0.999, 1e-15, 1)[0]
+    rr = TR.adam(rho, gr_u, np.zeros(n), np.zeros(n), 5e-2, 0.9, 0.999, 1e-15, 1)[0]
+    assert np.abs(ts.cpu().numpy() - rs).max() <= 2e-6
+    assert np.abs(tr_.cpu().numpy() - rr).max() <= 2e-6
+
+
+def test_fused_training_step_follows_the_unfused_one():
+    """The trainer's default step (scene-order gradients into the fused Adam
+    steps) against the step built from user-order gradients, separate
+    regulariser, Eq. 4 and Adam kernels: the same losses over a few
+    iterations and parameters that agree to float rounding."""
+    init, cams, images, rp, gt = T.synthetic_problem(n_sites=3000, n_cams=4, w=48, h=32, tex_res=4, seed=5)
+    out = {}
+    for fused in (True, False):
+        cfg = T.TrainConfig(iters=50, rays_per_iter=4096, refresh_every=0, vd_ramp_frac=0.0, seed=2,
+                            scene_order_grads=fused)
+        tr = T.Trainer(init["sites"], init["rho"], init["tex"], init["tex_vd"], cams, images, rp, cfg)
+        out[fused] = ([tr.step(sync_loss=True) for _ in range(4)], {k: v.clone() for k, v in tr.p.items()})
+        assert tr.scene.get_error()[0] == 0
+    (la, pa), (lb, pb) = out[True], out[False]
+    for a, b in zip(la, lb):
+        assert np.allclose(a, b, rtol=1e-4, atol=1e-7), (a, b)
+    for k in pa:
+        diff = (pa[k] - pb[k]).abs()
+        scale = (pb[k] - torch.as_tensor(init[k], device=DEV)).abs().max().item()  # size of the updates
+        # the gradient atomics sum in a different order on every run, so an
+        # entry whose gradient nearly cancels can take an Adam step of the
+        # other sign; all but a few entries agree to rounding
+        off = (diff > 1e-3 * scale + 1e-6).float().mean().item()
+        assert off <= 1e-4, (k, off, diff.max().item(), scale)
