@@ -412,8 +412,9 @@ vt_status vt_stream_read(const void* buf, int64_t bytes, int32_t reps, float* si
 /* Adam steps that take the gradients of vt_render_bwd_scene_order directly
  * (scene cell order, float4 records) and update user-order parameters, so a
  * training step needs no user-order gradient arrays. perm [N] is
- * vt_scene_permutation (scene cell k = user cell perm[k]); Adam as in
- * vt_adam_step (bias correction at `step`); all pointers DEVICE, FP32.
+ * vt_scene_permutation (scene cell k = user cell perm[k]; an entry outside
+ * [0, N) is skipped); Adam as in vt_adam_step (bias correction at `step`);
+ * all pointers DEVICE, FP32.
  *
  * Texture map: grad_tex_scene [N][R][R][4] (RGBA, A ignored); tex, m, v
  * [N][R][R][3] user order, updated in place. The map's regulariser of Eq. 5

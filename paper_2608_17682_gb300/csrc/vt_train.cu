@@ -151,7 +151,9 @@ __global__ void k_adam_tex_scene(int64_t n, int RR, const int32_t* __restrict__ 
   const float scale = 1.f / ((float)n * (float)RR);
   double acc = 0.0;
   for (int64_t k = warp0; k < n; k += warps) {
-    const int64_t base = (int64_t)perm[k] * RR * 3;
+    const int32_t uk = perm[k];
+    if (uk < 0 || (int64_t)uk >= n) continue;  // not a permutation entry: skipped (warp-uniform)
+    const int64_t base = (int64_t)uk * RR * 3;
     float m0 = 0.f, m1 = 0.f, m2 = 0.f;
     if (reg == 0 && lam != 0.f) {
       for (int t = lane; t < RR; t += 32) {
@@ -201,6 +203,7 @@ __global__ void k_adam_cells_scene(int64_t n, const int32_t* __restrict__ perm, 
                                    float c1, float c2) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t u = perm[k];
+    if (u < 0 || u >= n) continue;  // not a permutation entry: skipped
     const float4 g = gc[k];
     if (lr_s != 0.f) {
       const float gs[3] = {g.x, g.y, g.z};

@@ -123,10 +123,11 @@ def test_scene_order_texture_adam_matches_definition(reg):
     lam, lr = 0.3, 1e-2
     for k in range(1, 3):
         gsc = rng.normal(size=(n, R, R, 4)).astype(np.float32)
+        tgsc = torch.as_tensor(gsc, device=DEV)  # referenced until the kernel has run
         loss = torch.zeros(1, device=DEV)
-        _vt.vt_adam_step_tex_scene_order(n, R, tperm.data_ptr(), torch.as_tensor(gsc, device=DEV).data_ptr(),
-                                         tp.data_ptr(), tm.data_ptr(), tv.data_ptr(), reg, lam, lr, 0.9, 0.999, 1e-15, k,
-                                         loss.data_ptr(), _st())
+        _vt.vt_adam_step_tex_scene_order(n, R, tperm.data_ptr(), tgsc.data_ptr(), tp.data_ptr(), tm.data_ptr(),
+                                         tv.data_ptr(), reg, lam, lr, 0.9, 0.999, 1e-15, k, loss.data_ptr(), _st())
+        torch.cuda.synchronize()
         g_user = np.empty(p.shape)
         g_user[perm] = gsc[..., :3]
         if reg == 0:
@@ -151,10 +152,12 @@ def test_scene_order_cell_adam_matches_definition():
     ts, tr_ = torch.as_tensor(sites, device=DEV).clone(), torch.as_tensor(rho, device=DEV).clone()
     z = [torch.zeros(n, 3, device=DEV), torch.zeros(n, 3, device=DEV), torch.zeros(n, device=DEV),
          torch.zeros(n, device=DEV)]
-    _vt.vt_adam_step_cells_scene_order(n, torch.as_tensor(perm, device=DEV).data_ptr(),
-                                       torch.as_tensor(gc, device=DEV).data_ptr(), ts.data_ptr(), tr_.data_ptr(),
-                                       torch.as_tensor(sigma, device=DEV).data_ptr(), *[x.data_ptr() for x in z],
-                                       2e-3, 5e-2, 0.9, 0.999, 1e-15, 1, _st())
+    # every device array the kernel reads stays referenced until it has run
+    tperm, tgc, tsig = (torch.as_tensor(x, device=DEV) for x in (perm, gc, sigma))
+    _vt.vt_adam_step_cells_scene_order(n, tperm.data_ptr(), tgc.data_ptr(), ts.data_ptr(), tr_.data_ptr(),
+                                       tsig.data_ptr(), *[x.data_ptr() for x in z], 2e-3, 5e-2, 0.9, 0.999, 1e-15, 1,
+                                       _st())
+    torch.cuda.synchronize()
     gs_u = np.empty((n, 3))
     gs_u[perm] = gc[:, :3]
     gr_u = np.empty(n)
