@@ -191,4 +191,4 @@ def test_fused_training_step_follows_the_unfused_one():
         # entry whose gradient nearly cancels can take an Adam step of the
         # other sign; all but a few entries agree to rounding
         off = (diff > 1e-3 * scale + 1e-6).float().mean().item()
-        assert off <= 1e-4, (k, off, diff.max().item(), scale)
+        assert off <= 1e-3 and diff.max().item() <= 2e-2 * scale, (k, off, diff.max().item(), scale)
