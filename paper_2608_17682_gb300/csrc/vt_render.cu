@@ -1,8 +1,8 @@
 // vt_render.cu -- start-cell search, Voronoi walk, compositing, adjoint.
 //
 // One thread per ray; a warp covers a 4 x 8 tile of an image (the warp-coherent
-// tiling of Sec. 5.6, 8 pixels wide, 4 tall) and a 256-thread block a
-// 16 x 16-pixel patch of such tiles, so neighbouring threads walk similar
+// tiling of Sec. 5.6, 8 pixels wide, 4 tall) and a 128-thread block a
+// 16 x 8-pixel patch of such tiles, so neighbouring threads walk similar
 // cells and share cache lines. Forward, backward and trace are one templated
 // kernel whose walk is the same inline code, so their decisions are identical.
 //
@@ -37,9 +37,10 @@ namespace {
 
 enum Mode { FWD = 0, BWD = 1, TRACE = 2 };
 
-// minimum resident 256-thread blocks per SM requested for the walk kernels
-// (more warps hide the walk's dependent loads; the appearance-1 and
-// distortion backwards keep more registers for their adjoint state)
+// minimum resident warps per SM requested for the walk kernels, in units of
+// 8 warps (more warps hide the walk's dependent loads; the appearance-1 and
+// distortion backwards keep more registers for their adjoint state); the
+// launch bounds convert them to blocks of VT_WPB warps
 #ifndef VT_FWD_MINB
 #define VT_FWD_MINB 4
 #endif
@@ -70,13 +71,23 @@ enum Mode { FWD = 0, BWD = 1, TRACE = 2 };
 #ifndef VT_BWD_RELOAD_PREV
 #define VT_BWD_RELOAD_PREV 1
 #endif
-// tiles per row of the 8-tile patch a 256-thread block renders (8: a 64x4
-// pixel strip; 2: a 16x16 square). On 3M sites / 4 views: 8 327.6, 4 337.5,
-// 1 341.0, 2 346.0 Mrays/s fwd+bwd -- the squarest patch shares the most cells.
+// tiles per row of the patch a walk block renders (with 8-warp blocks, 8: a
+// 64x4 pixel strip; 2: a 16x16 square; on 3M sites / 4 views: 8 327.6, 4
+// 337.5, 1 341.0, 2 346.0 Mrays/s fwd+bwd -- the squarest patch shares the
+// most cells)
 #ifndef VT_ST_W
 #define VT_ST_W 2
 #endif
-constexpr int kPatchH = 8 / VT_ST_W;  // tile rows of a patch
+// warps per walk block (each warp a 4x8 tile; the block a patch of tiles).
+// On 3M sites / 4 views, walk kernels fwd / bwd in ms: 8 warps (16x16-pixel
+// patch) 3.16 / 5.11; 4 (16x8) 3.06 / 4.88; 2 (8x8) 3.08 / 4.91; 2 (16x4)
+// 3.14 / 5.01; 1 3.17 / 6.41: a smaller block leaves fewer lanes idle while
+// its slowest tile finishes.
+#ifndef VT_WPB
+#define VT_WPB 4
+#endif
+constexpr int kWpb = VT_WPB;
+constexpr int kPatchH = kWpb / VT_ST_W;  // tile rows of a patch
 // unroll factor of the neighbour loop
 #ifndef VT_NBR_UNROLL
 #define VT_NBR_UNROLL 8
@@ -526,9 +537,9 @@ __device__ __forceinline__ int64_t ray_of_thread(const RP& P, int64_t tid, int& 
     tiles_x = P.img[lo].tiles_x;
     first = P.img[lo].first_ray;
   }
-  // the 8 warps of a block take a VT_ST_W x kPatchH patch of tiles
+  // the kWpb warps of a block take a VT_ST_W x kPatchH patch of tiles
   const int st_x = P.layout == 1 ? P.st_x : P.img[img].st_x;
-  const int st = (int)(t >> 3), k = (int)(t & 7);
+  const int st = (int)(t / kWpb), k = (int)(t % kWpb);
   const int sy = st / st_x, sx = st - sy * st_x;
   const int tx = sx * VT_ST_W + k % VT_ST_W, ty = sy * kPatchH + k / VT_ST_W;
   if (tx >= tiles_x) return -1;
@@ -612,12 +623,12 @@ struct WalkBounds {
 };
 
 template <int MODE, int DT, int APP, int DIST, int HALF>
-__global__ void __launch_bounds__(256, WalkBounds<MODE, APP, DIST>::minb)
+__global__ void __launch_bounds__(kWpb * 32, WalkBounds<MODE, APP, DIST>::minb * 8 / kWpb)
     k_walk(Scene S, RP P, const float* __restrict__ O, const float* __restrict__ D,
            const int32_t* __restrict__ anchor_cell, float* __restrict__ rgb_out, float* __restrict__ T_out,
            int32_t* __restrict__ steps_out, Grad G, Trace TR) {
 #if VT_STAGE
-  __shared__ float4 stage[8][kStageCap];  // per warp: neighbour records of its shared cell
+  __shared__ float4 stage[kWpb][kStageCap];  // per warp: neighbour records of its shared cell
 #endif
   int anchor = 0;
   const int64_t ray = ray_of_thread(P, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, anchor);
@@ -1163,7 +1174,7 @@ vt_status make_rp(const vt_scene* s, int64_t n_rays, const vt_render_params* p, 
       e.st_x = (e.tiles_x + VT_ST_W - 1) / VT_ST_W;
       ray0 += (int64_t)w * h;
       // warps of this image: 8 per tile patch
-      tile0 += (int64_t)e.st_x * (((h + 3) / 4 + kPatchH - 1) / kPatchH) * 8;
+      tile0 += (int64_t)e.st_x * (((h + 3) / 4 + kPatchH - 1) / kPatchH) * kWpb;
     }
     if (ray0 != n_rays) return VT_ERR_INVALID_ARG;
     P.layout = 2;
@@ -1179,10 +1190,10 @@ vt_status make_rp(const vt_scene* s, int64_t n_rays, const vt_render_params* p, 
     per_image = (int64_t)p->img_w * p->img_h;
     if (per_image * p->n_images != n_rays) return VT_ERR_INVALID_ARG;
     P.tiles_x = (p->img_w + 7) / 8;
-    // warps per image: 8 per patch of VT_ST_W x kPatchH tiles (ragged patches
-    // at the right and bottom edges have idle warps)
+    // warps per image: kWpb per patch of VT_ST_W x kPatchH tiles (ragged
+    // patches at the right and bottom edges have idle warps)
     P.st_x = (P.tiles_x + VT_ST_W - 1) / VT_ST_W;
-    P.tiles_per_img = P.st_x * (((p->img_h + 3) / 4 + kPatchH - 1) / kPatchH) * 8;
+    P.tiles_per_img = P.st_x * (((p->img_h + 3) / 4 + kPatchH - 1) / kPatchH) * kWpb;
     int64_t groups = (p->n_images + VT_MAX_ANCHORS - 1) / VT_MAX_ANCHORS;
     P.anchor_stride = per_image * groups;
   } else {
@@ -1236,11 +1247,11 @@ void launch_walk_app(vt_scene* s, const Scene& S, const RP& P, const float* o, c
                      int32_t* steps, Grad G, Trace TR, cudaStream_t st, int g) {
   vt_note_launch();
   if (s->dtype == VT_F32)
-    k_walk<MODE, VT_F32, APP, DIST, HALF><<<g, 256, 0, st>>>(S, P, o, d, s->anchor_cell, rgb, T, steps, G, TR);
+    k_walk<MODE, VT_F32, APP, DIST, HALF><<<g, kWpb * 32, 0, st>>>(S, P, o, d, s->anchor_cell, rgb, T, steps, G, TR);
   else if (s->dtype == VT_F16)
-    k_walk<MODE, VT_F16, APP, DIST, HALF><<<g, 256, 0, st>>>(S, P, o, d, s->anchor_cell, rgb, T, steps, G, TR);
+    k_walk<MODE, VT_F16, APP, DIST, HALF><<<g, kWpb * 32, 0, st>>>(S, P, o, d, s->anchor_cell, rgb, T, steps, G, TR);
   else
-    k_walk<MODE, VT_BF16, APP, DIST, HALF><<<g, 256, 0, st>>>(S, P, o, d, s->anchor_cell, rgb, T, steps, G, TR);
+    k_walk<MODE, VT_BF16, APP, DIST, HALF><<<g, kWpb * 32, 0, st>>>(S, P, o, d, s->anchor_cell, rgb, T, steps, G, TR);
 }
 
 template <int MODE>
@@ -1248,7 +1259,7 @@ vt_status launch_walk_kernel(vt_scene* s, const Scene& S, const RP& P, const flo
                              float* T, int32_t* steps, Grad G, Trace TR, cudaStream_t st) {
   int64_t nt = walk_threads(P);
   if (nt == 0) return VT_OK;
-  int g = vt_grid(nt, 256, ((int64_t)1 << 31) - 1);
+  int g = vt_grid(nt, kWpb * 32, ((int64_t)1 << 31) - 1);
   constexpr int F = MODE == TRACE ? 0 : 1;  // no appearance / distortion variants of the trace
   const bool dist = MODE != TRACE && G.dist != nullptr;
   if (S.nbr_h) {
