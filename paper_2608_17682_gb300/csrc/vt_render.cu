@@ -37,21 +37,25 @@ namespace {
 
 enum Mode { FWD = 0, BWD = 1, TRACE = 2 };
 
-// minimum resident warps per SM requested for the walk kernels, in units of
-// 8 warps (more warps hide the walk's dependent loads; the appearance-1 and
-// distortion backwards keep more registers for their adjoint state); the
-// launch bounds convert them to blocks of VT_WPB warps
-#ifndef VT_FWD_MINB
-#define VT_FWD_MINB 4
+// minimum resident warps per SM requested for the walk kernels (more warps
+// hide the walk's dependent loads; the appearance-1 and distortion backwards
+// keep more registers for their adjoint state); the launch bounds convert
+// them to blocks of VT_WPB warps. On 3M sites / 4 views with 4-warp blocks:
+// forward 36 warps (56 registers) 3.01 ms, 32 (64) 3.07 ms, 40 (48) spills
+// twice as much; plain backward 24 warps (80 registers) 4.88 ms, 28 (72)
+// 4.88 ms, 20 (96, no spills) 5.08 ms; with 8-warp blocks the plain backward
+// ran 5.11 ms at 24 warps and 5.31 ms at 32.
+#ifndef VT_FWD_WARPS
+#define VT_FWD_WARPS 36
 #endif
-#ifndef VT_BWD_MINB
-// plain backward (appearance 0, no distortion): with the branch-free exit
-// search, 3 blocks/SM (80 registers) runs 5.11 ms against 5.31 ms at 4 (64
-// registers, more spills) on 3M sites / 4 views
-#define VT_BWD_MINB 3
+#ifndef VT_FWD_WARPS_EXT
+#define VT_FWD_WARPS_EXT 32  // forward with the paper's appearance model or the distortion loss
 #endif
-#ifndef VT_BWD_MINB_EXT
-#define VT_BWD_MINB_EXT 3  // backward with the paper's appearance model or the distortion loss
+#ifndef VT_BWD_WARPS
+#define VT_BWD_WARPS 24
+#endif
+#ifndef VT_BWD_WARPS_EXT
+#define VT_BWD_WARPS_EXT 24  // backward with the paper's appearance model or the distortion loss
 #endif
 // 1: issue a cell's texel loads before its exit search (latency overlapped,
 // more live registers); 0: after it
@@ -618,12 +622,14 @@ __device__ __forceinline__ void ff_fma_acc(float& hi, float& lo, float w, float 
 
 template <int MODE, int APP, int DIST>
 struct WalkBounds {
-  static constexpr int minb =
-      MODE == FWD ? VT_FWD_MINB : (MODE == BWD ? ((APP || DIST) ? VT_BWD_MINB_EXT : VT_BWD_MINB) : 2);
+  static constexpr int warps = MODE == FWD   ? ((APP || DIST) ? VT_FWD_WARPS_EXT : VT_FWD_WARPS)
+                               : MODE == BWD ? ((APP || DIST) ? VT_BWD_WARPS_EXT : VT_BWD_WARPS)
+                                             : 16;
+  static constexpr int blocks = warps / kWpb;  // resident blocks per SM requested
 };
 
 template <int MODE, int DT, int APP, int DIST, int HALF>
-__global__ void __launch_bounds__(kWpb * 32, WalkBounds<MODE, APP, DIST>::minb * 8 / kWpb)
+__global__ void __launch_bounds__(kWpb * 32, WalkBounds<MODE, APP, DIST>::blocks)
     k_walk(Scene S, RP P, const float* __restrict__ O, const float* __restrict__ D,
            const int32_t* __restrict__ anchor_cell, float* __restrict__ rgb_out, float* __restrict__ T_out,
            int32_t* __restrict__ steps_out, Grad G, Trace TR) {
