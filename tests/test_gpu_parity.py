@@ -1072,3 +1072,28 @@ def test_walk_events_time_the_kernel(medium):
     walk, call = ev[1].elapsed_time(ev[2]), ev[0].elapsed_time(ev[3])
     assert 0.0 < walk <= call
     assert ev[0].elapsed_time(ev[1]) >= 0.0 and ev[2].elapsed_time(ev[3]) >= 0.0
+
+
+def test_measurement_aids(tiny):
+    """vt_kernel_launches counts the library's own launches (a forward render:
+    anchor search, anchor refinement, walk); vt_stream_read reads a buffer
+    and rejects a misaligned pointer or size."""
+    from paper_2608_17682_gb300 import _vt
+    wl, osc, o, d = tiny
+    scene = api.Scene.from_workload(wl.scene)
+    to, td = to_dev(o, d)
+    P = gpu_params(wl.params, img_w=64, img_h=64, n_images=1)
+    api.render_fwd(scene, to, td, P)
+    before = _vt.vt_kernel_launches()
+    api.render_fwd(scene, to, td, P)
+    assert _vt.vt_kernel_launches() - before == 3
+    buf = torch.ones(1 << 20, device=DEV)
+    sink = torch.zeros(1, device=DEV)
+    st = torch.cuda.current_stream().cuda_stream
+    _vt.vt_stream_read(buf.data_ptr(), buf.numel() * 4, 3, sink.data_ptr(), st)
+    torch.cuda.synchronize()
+    assert sink.item() == 0.0  # written only on a value the data never produces
+    for ptr, nbytes in ((buf.data_ptr() + 4, 1024), (buf.data_ptr(), 1000)):
+        with pytest.raises(api._vt.VTError) as e:
+            _vt.vt_stream_read(ptr, nbytes, 1, sink.data_ptr(), st)
+        assert e.value.status == api._vt.VT_ERR_INVALID_ARG
