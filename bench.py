@@ -765,8 +765,9 @@ def run_ours(args, ws, rank, local):
         "gpu_launches_per_step": launches_per_step, "roofline": roof, **extra,
     }
     if rank == 0 and ws == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(args, wl, cams, args.cpu_seconds)
-        line["accuracy"] = accuracy_vs_oracle(args, wl, cams, scenes, dev)
+        # the oracle leg: the oracle timed on the host cores, and the timed
+        # kernels' error against it on a strided sample of the same rays
+        line["cpu_baseline"], line["accuracy"] = cpu_baseline(args, wl, cams, args.cpu_seconds, scenes, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -803,7 +804,17 @@ def oracle_step(osc, o, d, Y, params):
     O.render_bwd(osc, o, d, g, params=params)
 
 
-def cpu_baseline(args, wl, cams, seconds):
+def cpu_baseline(args, wl, cams, seconds, scenes=None, dev=None):
+    """The oracle leg of the benchmark: the FP64 oracle timed on a bounded
+    strided sample of the workload's rays on all host cores; with `scenes`,
+    also the accuracy of the timed kernels against the oracle
+    (accuracy_vs_oracle). Returns (cpu_baseline, accuracy or None)."""
+    base = _cpu_timing(args, wl, cams, seconds)
+    acc = accuracy_vs_oracle(args, wl, cams, scenes, dev) if scenes else None
+    return base, acc
+
+
+def _cpu_timing(args, wl, cams, seconds):
     osc, params = oracle_setup(args, wl)
     n = 64
     while True:

@@ -1,7 +1,8 @@
 """ctypes wrapper of the FP64 CPU oracle (``vt_oracle.c``).
 
 TEST INFRASTRUCTURE ONLY: imported by tests/, ``__graft_entry__.smoke()`` and
-bench.py's cpu_baseline / reference leg. The product library never imports it.
+bench.py's oracle leg (cpu_baseline with its accuracy check, and the reference
+arm). The product library never imports it.
 All inputs are promoted to float64 before the call (FP32 -> FP64 is exact).
 """
 from __future__ import annotations
